@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""GEMM throughput on GB300: C = 1.5 * A @ B + 0.5 * C at M = N = K = 8192.
+
+One step is one pass of the whole GEMM path through the C ABI: the BF16
+hi/lo split of A and of B, then the tensor-core 3xBF16 GEMM with its
+alpha/beta epilogue (or the selected --mode).  Inputs are seeded synthetic
+FP32 matrices, U[-1, 1] (A, B and the initial C), resident in HBM before
+timing; each of A, B, C is 268 MB, larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Prints ONE JSON line (rank 0).  `value` is effective TFLOP/s = 2MNK / t
+summed over all ranks; `e2e` is the same metric through gemm_from_host
+(pinned host buffers, copies inside the timed region); `roofline` rates the
+tensor-core kernel against the measured dense BF16 peak; `cpu_baseline` is
+the FP64 CPU oracle timed on the host cores on sampled rows; `compare`
+holds the FP32 SIMT kernel's throughput on the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16x3]
+    python bench.py --impl reference     # the CPU oracle arm
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GEMM TFLOP/s & % of peak at 8192^3: 3xBF16 TC vs FP32 SIMT, err<=1e-6"
+ALPHA, BETA = 1.5, 0.5
+SEED = 0x5EED
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="bf16x3", choices=["bf16x3", "bf16", "f32_simt"])
+    p.add_argument("--size", type=int, default=8192)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-compare", action="store_true", help="skip the FP32 SIMT comparison")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons (every 100 ms)."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                if self.uuid and parts[0] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        maxmhz = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        # samples taken while the GPU was busy (the clocks that matter)
+        busy = [float(r[1]) for r in rows
+                if r[3].replace(".", "").isdigit() and float(r[3]) > 250.0] or mhz
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": maxmhz,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------- helpers
+def dist_setup(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(n):
+    from paper_2305_18236_gb300 import inputs
+
+    A = inputs.uniform((n, n), SEED)
+    B = inputs.uniform((n, n), SEED + 1)
+    C0 = inputs.uniform((n, n), SEED + 2)
+    return A, B, C0
+
+
+def time_steps(fn, steps, warmup, world, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1)
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_rows_timed(A, B, C0, n, seconds, max_rows=4096):
+    """Time the FP64 oracle on evenly spaced rows of the workload, sized to
+    take about `seconds`.  Returns (rows, C64, D, elapsed, threads)."""
+    import numpy as np
+
+    import oracle
+
+    probe = np.linspace(0, n - 1, 4).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.gemm(A, B, ALPHA, BETA, C0, rows=probe)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    nrows = int(max(8, min(max_rows, seconds / max(per_row, 1e-6))))
+    rows = np.linspace(0, n - 1, nrows).astype(np.int64)
+    t0 = time.perf_counter()
+    C64, D, threads = oracle.gemm(A, B, ALPHA, BETA, C0, rows=rows)
+    el = time.perf_counter() - t0
+    return rows, C64, D, el, threads
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores, each step a
+    bounded sample of rows of the same 8192^3 workload."""
+    import numpy as np
+
+    import oracle
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.size
+    A, B, C0 = make_inputs(n)
+    probe = np.linspace(0, n - 1, 4).astype(np.int64)
+    t0 = time.perf_counter()
+    _, _, threads = oracle.gemm(A, B, ALPHA, BETA, C0, rows=probe)
+    per_row = (time.perf_counter() - t0) / 4
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rows_per_step = int(max(1, min(256, budget / max(per_row, 1e-6))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = (np.arange(rows_per_step) * 7919 + s * 104729) % n
+        t0 = time.perf_counter()
+        oracle.gemm(A, B, ALPHA, BETA, C0, rows=rows)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times)
+    flops = 2.0 * rows_per_step * n * n * args.steps
+    value = flops / t / 1e12
+    sample = "%d rows x %d cols x K=%d per step (FP64 triple loop, C and |A||B| sums)" % (
+        rows_per_step, n, n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5 U[-1,1]" % (n, n, n),
+                   "M": n, "N": n, "K": n, "sample_rows_per_step": rows_per_step},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    uuid = "GPU-" + str(props.uuid) if hasattr(props, "uuid") else None
+    n = args.size
+    M = N = K = n
+    A, B, C0 = make_inputs(n)
+    dA = torch.from_numpy(A).to(dev)
+    dB = torch.from_numpy(B).to(dev)
+    dC = torch.from_numpy(C0).to(dev)
+    h = g.Gemm(dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = args.mode
+    mcode = g.MODES[mode]
+    h.ensure_workspace(h.workspace_size(mcode, 0, 0, M, N, K))
+
+    def step(md=mcode):
+        st = h.gemm(0, 0, M, N, K, ALPHA, dA.data_ptr(), n, dB.data_ptr(), n, BETA,
+                    dC.data_ptr(), n, md)
+        if st != 0:
+            raise RuntimeError("gemm failed: %d" % st)
+
+    # launches per step, from the library's own count
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = h.last_launch_count()
+
+    sampler = ClockSampler(uuid)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler.start()
+    h.lib.gemm_profile_enable(h.h, 1)
+    ms = time_steps(step, args.steps, 0, world, stream)
+    import ctypes
+
+    main_ms, main_n = ctypes.c_double(), ctypes.c_int()
+    h.lib.gemm_profile_read(h.h, ctypes.byref(main_ms), ctypes.byref(main_n))
+    h.lib.gemm_profile_enable(h.h, 0)
+    clocks = sampler.stop()
+    if h.sync() != 0:
+        raise RuntimeError("kernel reported a bounded-wait timeout")
+    ms_max = max_over_ranks(ms, world)
+    flops = 2.0 * M * N * K
+    value = world * flops * args.steps / (ms_max / 1e3) / 1e12
+    kernel_ms = main_ms.value / max(1, main_n.value)
+
+    peaks, peak_src = load_peaks()
+    if mode == "f32_simt":
+        sm = props.multi_processor_count
+        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (kernel_ms / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": "%d SMs x 128 FP32 lanes x 2 x max clock" % sm}
+    else:
+        tensor_flops = flops * (3 if mode == "bf16x3" else 1)
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": tensor_flops / (kernel_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "%s dense BF16 (cuBLAS, sustained)" % peak_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms"] = kernel_ms
+
+    # FP32 SIMT comparison on the same workload
+    compare = None
+    if not args.no_compare and mode != "f32_simt":
+        simt_steps = max(3, min(10, args.steps))
+        ms_s = time_steps(lambda: step(g.MODES["f32_simt"]), simt_steps, 2, world, stream)
+        ms_s = max_over_ranks(ms_s, world)
+        simt = world * flops * simt_steps / (ms_s / 1e3) / 1e12
+        compare = {"f32_simt_tflops": simt, "speedup_vs_f32_simt": value / simt,
+                   "f32_simt_ms_per_step": ms_s / simt_steps}
+
+    # end to end through the public API with pinned host buffers
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.from_numpy(C0.copy()).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    for _ in range(2):
+        g.gemm_from_host(hA, hB, C=hC, alpha=ALPHA, beta=BETA, mode=mode, h=h)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.gemm_from_host(hA, hB, C=hC, alpha=ALPHA, beta=BETA, mode=mode, h=h)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * flops * e2e_steps / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+           "ms_per_step": 1000.0 * e2e_s / e2e_steps}
+    del hA, hB, hC
+
+    # CPU oracle baseline on sampled rows; the same rows give the error of a
+    # fresh GEMM (C = 1.5 A B + 0.5 C0) at this size
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rows, C64, D, el, threads = oracle_rows_timed(A, B, C0, n, args.cpu_seconds)
+        cpu = {"value": 2.0 * len(rows) * N * K / el / 1e12, "unit": "TFLOP/s",
+               "cores": threads, "kind": "oracle",
+               "sample": "%d evenly spaced rows of C (all %d columns, K=%d), FP64 triple loop"
+                         % (len(rows), N, K)}
+        import oracle
+
+        errs = {}
+        for md in ([mode] + (["f32_simt"] if mode != "f32_simt" else [])):
+            dC.copy_(torch.from_numpy(C0))
+            step(g.MODES[md])
+            torch.cuda.synchronize()
+            out = dC[torch.from_numpy(rows).to(dev)].cpu().numpy()
+            errs[md] = oracle.normwise_error(out, C64, D)
+        err = errs
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 (bf16 hi/lo products, f32 accumulate)",
+                  "bf16": "bf16 (f32 accumulate)", "f32_simt": "f32"}[mode],
+        "data": "synthetic",
+        "config": {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
+                               % (n, n, n),
+                   "mode": mode, "M": M, "N": N, "K": K, "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush",
+                   "launches_per_step": launches_per_step},
+        "roofline": roof,
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": e2e,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "compare": compare,
+        "normwise_error": err,
+        "peaks_source": peak_src,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * gb300 GEMM -- C ABI of a one-GPU GEMM library for NVIDIA GB300 (sm_103a).
+ *
+ * Every entry point computes (a piece of) the BLAS SGEMM contract that
+ * Kuzma et al., "Fast Matrix Multiplication via Compiler-only Layered Data
+ * Reorganization and Intrinsic Lowering" (SPE 2023) generate code for:
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C                     (Algorithm 1)
+ *
+ * Section 3 and Algorithm 1 define the operation: beta scales C once, alpha
+ * scales the accumulated product, op(X) is X or X^T ("access order",
+ * Section 3.2 end), ld* are the leading dimensions of the stored matrices.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Storage is ROW-MAJOR (the paper's matrices are column-major; a column-major
+ * caller computes C^T = op(B)^T op(A)^T, i.e. swaps A/B and M/N).
+ *   op(A) is M x K: A is stored M x K (transA == GEMM_OP_N) or K x M (GEMM_OP_T);
+ *   op(B) is K x N: B is stored K x N (transB == GEMM_OP_N) or N x K (GEMM_OP_T);
+ *   C is M x N.  ld* = distance in elements between consecutive stored rows,
+ *   and must be >= max(1, number of stored columns).
+ * Pointers named A, B, C, X, hi, lo, ws are DEVICE pointers unless the
+ * function says otherwise; the caller owns them.  `stream` is a cudaStream_t
+ * passed as void* (NULL = legacy default stream); all work is enqueued on
+ * it and nothing synchronises with the host unless stated.
+ * Errors are BLAS-style: an invalid argument returns GEMM_ERR_ARG, records
+ * its 1-based position (see gemm_last_error_arg) and launches nothing.
+ * Quick returns: M == 0 or N == 0 does nothing; K == 0 or alpha == 0 gives
+ * C <- beta * C without reading A or B; beta == 0 never reads C, so NaN or
+ * Inf already in C does not reach the result.
+ * A handle may be used by one host thread at a time.
+ */
+#ifndef GB300_GEMM_H
+#define GB300_GEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { GEMM_OP_N = 0, GEMM_OP_T = 1 } gemm_op_t;
+
+/* How op(A) op(B) is multiplied.
+ *  GEMM_MODE_F32_SIMT: FP32 fused multiply-adds on the CUDA cores (the
+ *    "generic lowering" of Section 3.2: plain vector FMA, no matrix engine).
+ *  GEMM_MODE_BF16: A and B rounded to BF16 (round to nearest even), products
+ *    on the tensor cores (tcgen05), FP32 accumulation.  The matrix-engine
+ *    lowering of Section 3.2 / Algorithm 2 with 16-bit inputs (rank-2
+ *    updates per element pair, Section 3.3).
+ *  GEMM_MODE_BF16X3: split-precision -- x = hi + lo with hi = bf16(x),
+ *    lo = bf16(x - hi); op(A) op(B) ~ Ahi Bhi + Ahi Blo + Alo Bhi on the
+ *    tensor cores with FP32 accumulation, recovering FP32-level accuracy.
+ *    Not in the paper. */
+typedef enum {
+    GEMM_MODE_F32_SIMT = 0,
+    GEMM_MODE_BF16 = 1,
+    GEMM_MODE_BF16X3 = 2
+} gemm_mode_t;
+
+typedef enum {
+    GEMM_OK = 0,
+    GEMM_ERR_ARG = -1,         /* invalid argument; position in gemm_last_error_arg */
+    GEMM_ERR_ALIGN = -2,       /* a tensor-core operand is not 16-byte aligned */
+    GEMM_ERR_WORKSPACE = -3,   /* caller workspace too small / allocation failed */
+    GEMM_ERR_CUDA = -4,        /* a CUDA runtime or driver call failed */
+    GEMM_ERR_TIMEOUT = -5,     /* a kernel's bounded wait expired (reported by gemm_sync) */
+    GEMM_ERR_UNSUPPORTED = -6, /* valid request this build cannot serve */
+    GEMM_ERR_DEVICE = -7       /* current device is not an sm_103 GPU */
+} gemm_status_t;
+
+typedef struct gemm_context *gemm_handle_t;
+
+/* Launch configuration overrides (all 0 = library choice).
+ *  bn:        tensor-core tile width in N (128 or 256); the tile height is 128.
+ *  bk:        K depth of one pipeline stage (32 or 64 BF16 elements).
+ *  stages:    shared-memory ring depth (2..8; clamped to what fits).
+ *  split_k:   number of K slices reduced by a second kernel (1 = none).
+ *  raster_group: number of M tiles walked together before moving along N.
+ *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).
+ *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
+ *    the device error word and exits cleanly (0 = default, about seconds). */
+typedef struct {
+    int32_t bn;
+    int32_t bk;
+    int32_t stages;
+    int32_t split_k;
+    int32_t raster_group;
+    int32_t max_ctas;
+    int64_t wait_poll_limit;
+} gemm_config_t;
+
+/* Create a handle bound to the CURRENT CUDA device.  Allocates a 256-byte
+ * device error word.  Returns GEMM_ERR_DEVICE if the device is not sm_103,
+ * GEMM_ERR_ARG (arg 1) if handle is NULL. */
+gemm_status_t gemm_create(gemm_handle_t *handle);
+
+/* Free the handle, its error word and any workspace it allocated itself.
+ * Synchronises the device first.  NULL is accepted. */
+gemm_status_t gemm_destroy(gemm_handle_t handle);
+
+/* Override (cfg != NULL) or reset (cfg == NULL) the launch configuration.
+ * Invalid fields give GEMM_ERR_ARG with position 2. */
+gemm_status_t gemm_set_config(gemm_handle_t handle, const gemm_config_t *cfg);
+
+/* Bytes of device workspace gemm() needs for this problem and mode with the
+ * handle's current configuration (0 for GEMM_MODE_F32_SIMT, except with
+ * split-K).  Workspace holds the BF16 split/packed operands (Algorithm 1's
+ * APack/BPack buffers) and split-K partial sums.  Returns 0 for invalid
+ * arguments. */
+size_t gemm_workspace_size(gemm_handle_t handle, gemm_mode_t mode, gemm_op_t transA,
+                           gemm_op_t transB, int64_t M, int64_t N, int64_t K);
+
+/* Give the handle caller-owned device workspace (256-byte aligned, or
+ * GEMM_ERR_ALIGN).  The caller keeps ownership and must keep it alive until
+ * the work using it has finished on the stream.  ws == NULL returns to the
+ * handle's own workspace, which it grows with cudaMalloc on demand. */
+gemm_status_t gemm_set_workspace(gemm_handle_t handle, void *ws, size_t bytes);
+
+/* C <- alpha * op(A) op(B) + beta * C, FP32 in and out, device pointers,
+ * computed as `mode` says.  Argument positions for GEMM_ERR_ARG:
+ * 1 handle, 2 transA, 3 transB, 4 M, 5 N, 6 K, 7 alpha, 8 A, 9 lda, 10 B,
+ * 11 ldb, 12 beta, 13 C, 14 ldc, 15 mode, 16 stream.
+ * A, B, C may have any 4-byte alignment and any valid ld.
+ * With a tensor-core mode and no caller workspace, the first call of a new
+ * largest size allocates (cudaMalloc) and is therefore not graph-capturable. */
+gemm_status_t gemm(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
+                   int64_t M, int64_t N, int64_t K,
+                   float alpha, const float *A, int64_t lda,
+                   const float *B, int64_t ldb,
+                   float beta, float *C, int64_t ldc,
+                   gemm_mode_t mode, void *stream);
+
+/* C <- alpha * op(A) op(B) + beta * C with BF16 A and B (uint16_t bit
+ * patterns), FP32 C, tensor cores with FP32 accumulation.  Operands that
+ * are already K-contiguous (transA == N, transB == T) are read in place and
+ * need a 16-byte aligned base and ld % 8 == 0 (else GEMM_ERR_ALIGN); the
+ * others are first packed K-contiguous into workspace (Algorithm 1's
+ * pack step).  Argument positions as for gemm() (no mode; 15 is stream). */
+gemm_status_t gemm_bf16(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
+                        int64_t M, int64_t N, int64_t K,
+                        float alpha, const uint16_t *A, int64_t lda,
+                        const uint16_t *B, int64_t ldb,
+                        float beta, float *C, int64_t ldc, void *stream);
+
+/* The split step on its own: Y = op(X) (rows x cols, X stored row-major
+ * with row stride ldx, op as `trans`), written as hi = bf16_rne(Y) and
+ * lo = bf16_rne(Y - hi) (lo = 0 where hi is not finite) with row stride
+ * ldo elements.  lo may be NULL (hi only).  hi and lo must be 16-byte
+ * aligned and ldo % 8 == 0 (GEMM_ERR_ALIGN).  Positions: 1 handle,
+ * 2 trans, 3 rows, 4 cols, 5 X, 6 ldx, 7 hi, 8 lo, 9 ldo, 10 stream. */
+gemm_status_t gemm_split_bf16(gemm_handle_t handle, gemm_op_t trans, int64_t rows, int64_t cols,
+                              const float *X, int64_t ldx, uint16_t *hi, uint16_t *lo,
+                              int64_t ldo, void *stream);
+
+/* gemm() on HOST buffers: copies A, B (and C when beta != 0) to device
+ * buffers the handle owns (grown with cudaMalloc on demand), runs gemm() on
+ * `stream`, copies C back and synchronises the stream.  Pinned host memory
+ * gives asynchronous copies; pageable memory works but is slower.  Also
+ * reports a kernel's bounded-wait expiry (GEMM_ERR_TIMEOUT).  Positions as
+ * for gemm(). */
+gemm_status_t gemm_from_host(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
+                             int64_t M, int64_t N, int64_t K,
+                             float alpha, const float *A, int64_t lda,
+                             const float *B, int64_t ldb,
+                             float beta, float *C, int64_t ldc,
+                             gemm_mode_t mode, void *stream);
+
+/* One problem of a grouped call: C_g <- alpha_g op(A_g) op(B_g) + beta_g C_g. */
+typedef struct {
+    int64_t M, N, K;
+    int64_t lda, ldb, ldc;
+    const float *A;
+    const float *B;
+    float *C;
+    float alpha, beta;
+    int32_t transA, transB; /* gemm_op_t values */
+} gemm_problem_t;
+
+/* Many independent FP32 GEMMs in one call (split passes plus one persistent
+ * tensor-core launch over all problems' tiles).  host_problems (HOST
+ * memory, `count` entries) describe the problems; their pointers are
+ * device pointers.  Supports GEMM_MODE_BF16 and GEMM_MODE_BF16X3.  Not in
+ * the paper; the per-problem tile parameters play the role of its
+ * per-target mc/kc/nc blocking (Section 3.1, Eqs. 1-7).  Positions:
+ * 1 handle, 2 mode, 3 host_problems (index of the first bad problem is
+ * reported as 100 + problem index), 4 count, 5 stream. */
+gemm_status_t gemm_grouped(gemm_handle_t handle, gemm_mode_t mode,
+                           const gemm_problem_t *host_problems, int32_t count, void *stream);
+
+/* Gradients of C = op(A) op(B) (alpha = 1, beta = 0) for a given dC:
+ *   dA = dC op(B)^T  (stored like A: M x K, or K x M when transA == T),
+ *   dB = op(A)^T dC  (stored like B).
+ * dA or dB may be NULL to skip it.  Not in the paper.  Positions:
+ * 1 handle, 2 transA, 3 transB, 4 M, 5 N, 6 K, 7 dC, 8 lddc, 9 A, 10 lda,
+ * 11 B, 12 ldb, 13 dA, 14 ldda, 15 dB, 16 lddb, 17 mode, 18 stream. */
+gemm_status_t gemm_backward(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
+                            int64_t M, int64_t N, int64_t K,
+                            const float *dC, int64_t lddc,
+                            const float *A, int64_t lda, const float *B, int64_t ldb,
+                            float *dA, int64_t ldda, float *dB, int64_t lddb,
+                            gemm_mode_t mode, void *stream);
+
+/* Benchmark hook.  While enabled, every call records a pair of CUDA events
+ * around its main GEMM kernel (the tensor-core or SIMT kernel, not the
+ * split/pack or reduce kernels) on the call's stream.  Not in the paper. */
+gemm_status_t gemm_profile_enable(gemm_handle_t handle, int enable);
+
+/* Synchronise on the recorded events and return the summed duration of the
+ * main kernels recorded since enabling or the last read (milliseconds) and
+ * their number; then forget them. */
+gemm_status_t gemm_profile_read(gemm_handle_t handle, double *main_ms, int *main_launches);
+
+/* Synchronise `stream`, then read and clear the handle's device error word:
+ * GEMM_ERR_TIMEOUT if a kernel abandoned a bounded wait since the last
+ * check, GEMM_ERR_CUDA if the stream reported an error, else GEMM_OK. */
+gemm_status_t gemm_sync(gemm_handle_t handle, void *stream);
+
+/* 1-based position of the invalid argument of the handle's last call
+ * (0 if the last call succeeded or failed for another reason). */
+int gemm_last_error_arg(gemm_handle_t handle);
+
+/* Number of kernels the handle's last successful call enqueued. */
+int gemm_last_launch_count(gemm_handle_t handle);
+
+/* Static text for a status code. */
+const char *gemm_status_string(gemm_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_GEMM_H */

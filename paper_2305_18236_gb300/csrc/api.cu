@@ -1,0 +1,595 @@
+// C ABI of the GEMM library (declarations and contracts in include/gemm.h).
+//
+// Host-side work only: argument checks (BLAS xerbla style), quick returns,
+// workspace planning, the launch plan, and dispatch to the kernels.  Every
+// arithmetic step of C = alpha op(A) op(B) + beta C runs in a CUDA kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gemm.h"
+#include "internal.h"
+
+struct gemm_context {
+    int device = 0;
+    int num_sms = 0;
+    int* err_word = nullptr;  // device, 256 bytes
+    void* own_ws = nullptr;
+    size_t own_ws_bytes = 0;
+    void* user_ws = nullptr;
+    size_t user_ws_bytes = 0;
+    gemm_config_t cfg{};
+    int last_err_arg = 0;
+    int last_launches = 0;
+    // device staging for gemm_from_host
+    float* hA = nullptr;
+    float* hB = nullptr;
+    float* hC = nullptr;
+    size_t hA_bytes = 0, hB_bytes = 0, hC_bytes = 0;
+    // benchmark hook: event pairs around main kernels
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;  // 2 per recorded launch
+    size_t ev_used = 0;
+};
+
+namespace {
+
+using gb300::TcLaunch;
+using gb300::TcOperand;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int64_t round8(int64_t k) { return (k + 7) / 8 * 8; }
+
+gemm_status_t fail_arg(gemm_context* h, int pos) {
+    if (h) h->last_err_arg = pos;
+    return GEMM_ERR_ARG;
+}
+
+// Stored-matrix geometry check: rows x cols stored with row stride ld.
+bool ld_ok(int64_t ld, int64_t cols) { return ld >= std::max<int64_t>(1, cols); }
+
+TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K) {
+    TcLaunch c;
+    c.bn = h->cfg.bn ? h->cfg.bn : 256;
+    c.bk = h->cfg.bk ? h->cfg.bk : (nterms == 3 ? 32 : 64);
+    c.stages = h->cfg.stages;
+    c.raster_group = h->cfg.raster_group ? h->cfg.raster_group : 16;
+    c.max_ctas = h->cfg.max_ctas;
+    c.poll_limit = h->cfg.wait_poll_limit;
+    if (h->cfg.split_k > 0) {
+        c.split_k = h->cfg.split_k;
+    } else {
+        // Few output tiles and a long K: slice K so every SM gets work.
+        const int64_t tiles = ((M + 127) / 128) * ((N + c.bn - 1) / c.bn);
+        const int64_t kblocks = (K + c.bk - 1) / c.bk;
+        int64_t split = 1;
+        if (tiles * 2 <= h->num_sms && kblocks >= 16)
+            split = std::min<int64_t>({h->num_sms / std::max<int64_t>(tiles, 1), kblocks / 8, 16});
+        c.split_k = int(std::max<int64_t>(split, 1));
+    }
+    return c;
+}
+
+struct WsPlan {
+    size_t a_off = 0, b_off = 0, p_off = 0, total = 0;
+    int64_t kp = 0;
+    int planes = 1;
+    int split = 1;
+};
+
+// Workspace of a tensor-core call: packed A (planes x M x Kp BF16), packed B
+// (planes x N x Kp BF16), split-K partials (split x M x N FP32).
+WsPlan plan_ws(int planes, bool pack_a, bool pack_b, int64_t M, int64_t N, int64_t K,
+               const TcLaunch& c) {
+    WsPlan w;
+    w.kp = round8(K);
+    w.planes = planes;
+    size_t off = 0;
+    if (pack_a) {
+        w.a_off = off;
+        off += align_up(size_t(planes) * M * w.kp * 2);
+    }
+    if (pack_b) {
+        w.b_off = off;
+        off += align_up(size_t(planes) * N * w.kp * 2);
+    }
+    const int64_t kblocks = (K + c.bk - 1) / c.bk;
+    int split = std::max(1, std::min<int>(c.split_k, int(std::max<int64_t>(kblocks, 1))));
+    if (split > 1) {
+        const int64_t per = (kblocks + split - 1) / split;
+        split = int((kblocks + per - 1) / per);
+    }
+    w.split = split;
+    if (split > 1) {
+        w.p_off = off;
+        off += align_up(size_t(split) * M * N * 4);
+    }
+    w.total = off;
+    return w;
+}
+
+// Workspace pointer of at least `bytes`, from the caller or the handle.
+gemm_status_t get_ws(gemm_context* h, size_t bytes, uint8_t** out) {
+    *out = nullptr;
+    if (bytes == 0) return GEMM_OK;
+    if (h->user_ws) {
+        if (h->user_ws_bytes < bytes) return GEMM_ERR_WORKSPACE;
+        *out = static_cast<uint8_t*>(h->user_ws);
+        return GEMM_OK;
+    }
+    if (h->own_ws_bytes < bytes) {
+        if (h->own_ws) {
+            cudaDeviceSynchronize();  // earlier work may still use the old buffer
+            cudaFree(h->own_ws);
+            h->own_ws = nullptr;
+            h->own_ws_bytes = 0;
+        }
+        if (cudaMalloc(&h->own_ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return GEMM_ERR_WORKSPACE;
+        }
+        h->own_ws_bytes = bytes;
+    }
+    *out = static_cast<uint8_t*>(h->own_ws);
+    return GEMM_OK;
+}
+
+// Event pair bracketing the next main-kernel launch (profiling only).
+cudaEvent_t* prof_slot(gemm_context* h) {
+    if (!h->profiling) return nullptr;
+    if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            h->ev_pool.push_back(e);
+        }
+    }
+    cudaEvent_t* p = &h->ev_pool[h->ev_used];
+    h->ev_used += 2;
+    return p;
+}
+
+struct ProfScope {
+    cudaEvent_t* ev;
+    cudaStream_t s;
+    ProfScope(gemm_context* h, cudaStream_t st) : ev(prof_slot(h)), s(st) {
+        if (ev) cudaEventRecord(ev[0], s);
+    }
+    ~ProfScope() {
+        if (ev) cudaEventRecord(ev[1], s);
+    }
+};
+
+gemm_status_t status_of(cudaError_t e) { return e == cudaSuccess ? GEMM_OK : GEMM_ERR_CUDA; }
+
+gemm_status_t check_common(gemm_context* h, int transA, int transB, int64_t M, int64_t N,
+                           int64_t K, float alpha, const void* A, int64_t lda, const void* B,
+                           int64_t ldb, const void* C, int64_t ldc) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    if (transA != GEMM_OP_N && transA != GEMM_OP_T) return fail_arg(h, 2);
+    if (transB != GEMM_OP_N && transB != GEMM_OP_T) return fail_arg(h, 3);
+    if (M < 0) return fail_arg(h, 4);
+    if (N < 0) return fail_arg(h, 5);
+    if (K < 0) return fail_arg(h, 6);
+    const bool reads_ab = M > 0 && N > 0 && K > 0 && alpha != 0.0f;
+    if (reads_ab && !A) return fail_arg(h, 8);
+    if (!ld_ok(lda, transA ? M : K)) return fail_arg(h, 9);
+    if (reads_ab && !B) return fail_arg(h, 10);
+    if (!ld_ok(ldb, transB ? K : N)) return fail_arg(h, 11);
+    if (M > 0 && N > 0 && !C) return fail_arg(h, 13);
+    if (!ld_ok(ldc, N)) return fail_arg(h, 14);
+    return GEMM_OK;
+}
+
+bool too_large(int64_t M, int64_t N, int64_t K) {
+    const int64_t lim = (int64_t(1) << 31) - 1024;
+    return M > lim || N > lim || K > lim;
+}
+
+gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                       float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                       float beta, float* C, int64_t ldc, int mode, cudaStream_t s) {
+    h->last_launches = 0;
+    if (M == 0 || N == 0) return GEMM_OK;
+    if (K == 0 || alpha == 0.0f) {
+        h->last_launches = 1;
+        return status_of(gb300::launch_scale_c(M, N, beta, C, ldc, s));
+    }
+    if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
+    if (mode == GEMM_MODE_F32_SIMT) {
+        h->last_launches = 1;
+        ProfScope prof(h, s);
+        return status_of(
+            gb300::launch_simt_f32(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s));
+    }
+    const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
+    const int planes = nterms == 3 ? 2 : 1;
+    const TcLaunch cfg = plan_tc(h, nterms, M, N, K);
+    const WsPlan w = plan_ws(planes, true, true, M, N, K, cfg);
+    uint8_t* ws;
+    gemm_status_t st = get_ws(h, w.total, &ws);
+    if (st != GEMM_OK) return st;
+    uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
+    uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
+    const int64_t a_plane = M * w.kp, b_plane = N * w.kp;
+    // pack/split op(A) as M x K and op(B)^T as N x K, both K-contiguous
+    if (gb300::launch_split_bf16(transA, M, K, A, lda, a_hi, planes > 1 ? a_hi + a_plane : nullptr,
+                                 w.kp, s) != cudaSuccess)
+        return GEMM_ERR_CUDA;
+    if (gb300::launch_split_bf16(!transB, N, K, B, ldb, b_hi, planes > 1 ? b_hi + b_plane : nullptr,
+                                 w.kp, s) != cudaSuccess)
+        return GEMM_ERR_CUDA;
+    TcOperand oa{a_hi, M, K, w.kp, a_plane, planes};
+    TcOperand ob{b_hi, N, K, w.kp, b_plane, planes};
+    TcLaunch c2 = cfg;
+    c2.split_k = w.split;
+    float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
+    int launches = 2;
+    int rc;
+    {
+        ProfScope prof(h, s);
+        rc = gb300::launch_tc_gemm(oa, ob, nterms, M, N, K, alpha, beta, C, ldc, partial, c2,
+                                   h->err_word, h->num_sms, s, &launches);
+    }
+    if (rc != 0) return static_cast<gemm_status_t>(rc);
+    h->last_launches = launches;
+    return GEMM_OK;
+}
+
+gemm_status_t grow(float** p, size_t* have, size_t want) {
+    if (*have >= want) return GEMM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(p), want) != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_WORKSPACE;
+    }
+    *have = want;
+    return GEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gemm_status_t gemm_create(gemm_handle_t* handle) {
+    if (!handle) return GEMM_ERR_ARG;
+    *handle = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_DEVICE;
+    }
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3) return GEMM_ERR_DEVICE;
+    gemm_context* h = new (std::nothrow) gemm_context();
+    if (!h) return GEMM_ERR_WORKSPACE;
+    h->device = dev;
+    h->num_sms = sms;
+    if (cudaMalloc(reinterpret_cast<void**>(&h->err_word), 256) != cudaSuccess ||
+        cudaMemset(h->err_word, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return GEMM_ERR_CUDA;
+    }
+    *handle = h;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_destroy(gemm_handle_t h) {
+    if (!h) return GEMM_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->err_word);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_ws) cudaFree(h->own_ws);
+    if (h->hA) cudaFree(h->hA);
+    if (h->hB) cudaFree(h->hB);
+    if (h->hC) cudaFree(h->hC);
+    delete h;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    if (!cfg) {
+        h->cfg = gemm_config_t{};
+        return GEMM_OK;
+    }
+    const gemm_config_t& c = *cfg;
+    if ((c.bn != 0 && c.bn != 128 && c.bn != 256) || (c.bk != 0 && c.bk != 32 && c.bk != 64) ||
+        c.stages < 0 || c.stages > 8 || c.stages == 1 || c.split_k < 0 || c.split_k > 64 ||
+        c.raster_group < 0 || c.max_ctas < 0 || c.wait_poll_limit < 0)
+        return fail_arg(h, 2);
+    h->cfg = c;
+    return GEMM_OK;
+}
+
+size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, gemm_op_t transB,
+                           int64_t M, int64_t N, int64_t K) {
+    if (!h || M < 0 || N < 0 || K < 0) return 0;
+    if (M == 0 || N == 0 || K == 0 || mode == GEMM_MODE_F32_SIMT) return 0;
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
+    (void)transA;
+    (void)transB;
+    const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
+    const TcLaunch c = plan_tc(h, nterms, M, N, K);
+    return plan_ws(nterms == 3 ? 2 : 1, true, true, M, N, K, c).total;
+}
+
+gemm_status_t gemm_set_workspace(gemm_handle_t h, void* ws, size_t bytes) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    if (ws && (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0) return GEMM_ERR_ALIGN;
+    h->user_ws = ws;
+    h->user_ws_bytes = ws ? bytes : 0;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int64_t M, int64_t N,
+                   int64_t K, float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                   float beta, float* C, int64_t ldc, gemm_mode_t mode, void* stream) {
+    gemm_status_t st = check_common(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, C, ldc);
+    if (st != GEMM_OK) return st;
+    if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3)
+        return fail_arg(h, 15);
+    return run_gemm(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode,
+                    static_cast<cudaStream_t>(stream));
+}
+
+gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int64_t M, int64_t N,
+                        int64_t K, float alpha, const uint16_t* A, int64_t lda, const uint16_t* B,
+                        int64_t ldb, float beta, float* C, int64_t ldc, void* stream) {
+    gemm_status_t st = check_common(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, C, ldc);
+    if (st != GEMM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    h->last_launches = 0;
+    if (M == 0 || N == 0) return GEMM_OK;
+    if (K == 0 || alpha == 0.0f) {
+        h->last_launches = 1;
+        return status_of(gb300::launch_scale_c(M, N, beta, C, ldc, s));
+    }
+    if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
+    // K-contiguous operands are read in place by TMA; the rest are packed.
+    const bool pack_a = transA == GEMM_OP_T;
+    const bool pack_b = transB == GEMM_OP_N;
+    if (!pack_a && ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 8))) return GEMM_ERR_ALIGN;
+    if (!pack_b && ((reinterpret_cast<uintptr_t>(B) & 15) || (ldb % 8))) return GEMM_ERR_ALIGN;
+    const TcLaunch cfg = plan_tc(h, 1, M, N, K);
+    const WsPlan w = plan_ws(1, pack_a, pack_b, M, N, K, cfg);
+    uint8_t* ws;
+    st = get_ws(h, w.total, &ws);
+    if (st != GEMM_OK) return st;
+    int launches = 0;
+    TcOperand oa{A, M, K, lda, M * lda, 1};
+    TcOperand ob{B, N, K, ldb, N * ldb, 1};
+    if (pack_a) {
+        uint16_t* pa = reinterpret_cast<uint16_t*>(ws + w.a_off);
+        if (gb300::launch_pack_bf16(1, M, K, A, lda, pa, w.kp, s) != cudaSuccess) return GEMM_ERR_CUDA;
+        oa = TcOperand{pa, M, K, w.kp, M * w.kp, 1};
+        ++launches;
+    }
+    if (pack_b) {
+        uint16_t* pb = reinterpret_cast<uint16_t*>(ws + w.b_off);
+        if (gb300::launch_pack_bf16(1, N, K, B, ldb, pb, w.kp, s) != cudaSuccess) return GEMM_ERR_CUDA;
+        ob = TcOperand{pb, N, K, w.kp, N * w.kp, 1};
+        ++launches;
+    }
+    TcLaunch c2 = cfg;
+    c2.split_k = w.split;
+    float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
+    int rc;
+    {
+        ProfScope prof(h, s);
+        rc = gb300::launch_tc_gemm(oa, ob, 1, M, N, K, alpha, beta, C, ldc, partial, c2,
+                                   h->err_word, h->num_sms, s, &launches);
+    }
+    if (rc != 0) return static_cast<gemm_status_t>(rc);
+    h->last_launches = launches;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_split_bf16(gemm_handle_t h, gemm_op_t trans, int64_t rows, int64_t cols,
+                              const float* X, int64_t ldx, uint16_t* hi, uint16_t* lo, int64_t ldo,
+                              void* stream) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    h->last_launches = 0;
+    if (trans != GEMM_OP_N && trans != GEMM_OP_T) return fail_arg(h, 2);
+    if (rows < 0) return fail_arg(h, 3);
+    if (cols < 0) return fail_arg(h, 4);
+    const bool any = rows > 0 && cols > 0;
+    if (any && !X) return fail_arg(h, 5);
+    if (!ld_ok(ldx, trans ? rows : cols)) return fail_arg(h, 6);
+    if (any && !hi) return fail_arg(h, 7);
+    if (!ld_ok(ldo, cols)) return fail_arg(h, 9);
+    if ((reinterpret_cast<uintptr_t>(hi) & 15) || (reinterpret_cast<uintptr_t>(lo) & 15) ||
+        (ldo % 8))
+        return GEMM_ERR_ALIGN;
+    if (!any) return GEMM_OK;
+    h->last_launches = 1;
+    return status_of(gb300::launch_split_bf16(trans, rows, cols, X, ldx, hi, lo, ldo,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int64_t M,
+                             int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                             const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                             gemm_mode_t mode, void* stream) {
+    gemm_status_t st = check_common(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, C, ldc);
+    if (st != GEMM_OK) return st;
+    if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3)
+        return fail_arg(h, 15);
+    if (M == 0 || N == 0) return GEMM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool reads_ab = K > 0 && alpha != 0.0f;
+    const int64_t ar = transA ? K : M, ac = transA ? M : K;
+    const int64_t br = transB ? N : K, bc = transB ? K : N;
+    if (reads_ab) {
+        if ((st = grow(&h->hA, &h->hA_bytes, size_t(ar) * lda * 4)) != GEMM_OK) return st;
+        if ((st = grow(&h->hB, &h->hB_bytes, size_t(br) * ldb * 4)) != GEMM_OK) return st;
+        if (cudaMemcpy2DAsync(h->hA, lda * 4, A, lda * 4, ac * 4, ar, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemcpy2DAsync(h->hB, ldb * 4, B, ldb * 4, bc * 4, br, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess)
+            return GEMM_ERR_CUDA;
+    }
+    if ((st = grow(&h->hC, &h->hC_bytes, size_t(M) * ldc * 4)) != GEMM_OK) return st;
+    if (beta != 0.0f &&
+        cudaMemcpy2DAsync(h->hC, ldc * 4, C, ldc * 4, N * 4, M, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return GEMM_ERR_CUDA;
+    st = run_gemm(h, transA, transB, M, N, K, alpha, h->hA, lda, h->hB, ldb, beta, h->hC, ldc, mode,
+                  s);
+    if (st != GEMM_OK) return st;
+    if (cudaMemcpy2DAsync(C, ldc * 4, h->hC, ldc * 4, N * 4, M, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return GEMM_ERR_CUDA;
+    const int launches = h->last_launches;
+    st = gemm_sync(h, stream);
+    h->last_launches = launches;
+    return st;
+}
+
+gemm_status_t gemm_grouped(gemm_handle_t h, gemm_mode_t mode, const gemm_problem_t* host_problems,
+                           int32_t count, void* stream) {
+    (void)stream;
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return fail_arg(h, 2);
+    if (count < 0) return fail_arg(h, 4);
+    if (count > 0 && !host_problems) return fail_arg(h, 3);
+    return GEMM_ERR_UNSUPPORTED;
+}
+
+gemm_status_t gemm_backward(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int64_t M,
+                            int64_t N, int64_t K, const float* dC, int64_t lddc, const float* A,
+                            int64_t lda, const float* B, int64_t ldb, float* dA, int64_t ldda,
+                            float* dB, int64_t lddb, gemm_mode_t mode, void* stream) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    if (transA != GEMM_OP_N && transA != GEMM_OP_T) return fail_arg(h, 2);
+    if (transB != GEMM_OP_N && transB != GEMM_OP_T) return fail_arg(h, 3);
+    if (M < 0) return fail_arg(h, 4);
+    if (N < 0) return fail_arg(h, 5);
+    if (K < 0) return fail_arg(h, 6);
+    const bool any = M > 0 && N > 0 && K > 0;
+    if (any && !dC) return fail_arg(h, 7);
+    if (!ld_ok(lddc, N)) return fail_arg(h, 8);
+    if (any && dA == nullptr && dB == nullptr) return GEMM_OK;
+    if (any && dB && !A) return fail_arg(h, 9);
+    if (!ld_ok(lda, transA ? M : K)) return fail_arg(h, 10);
+    if (any && dA && !B) return fail_arg(h, 11);
+    if (!ld_ok(ldb, transB ? K : N)) return fail_arg(h, 12);
+    if (dA && !ld_ok(ldda, transA ? M : K)) return fail_arg(h, 14);
+    if (dB && !ld_ok(lddb, transB ? K : N)) return fail_arg(h, 16);
+    if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3)
+        return fail_arg(h, 17);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int total = 0;
+    gemm_status_t st = GEMM_OK;
+    if (dA) {
+        // dA = dC op(B)^T (M x K); stored transposed when transA == T.
+        if (transA == GEMM_OP_N)
+            st = run_gemm(h, GEMM_OP_N, !transB, M, K, N, 1.0f, dC, lddc, B, ldb, 0.0f, dA, ldda,
+                          mode, s);
+        else
+            st = run_gemm(h, transB, GEMM_OP_T, K, M, N, 1.0f, B, ldb, dC, lddc, 0.0f, dA, ldda,
+                          mode, s);
+        if (st != GEMM_OK) return st;
+        total += h->last_launches;
+    }
+    if (dB) {
+        // dB = op(A)^T dC (K x N); stored transposed when transB == T.
+        if (transB == GEMM_OP_N)
+            st = run_gemm(h, !transA, GEMM_OP_N, K, N, M, 1.0f, A, lda, dC, lddc, 0.0f, dB, lddb,
+                          mode, s);
+        else
+            st = run_gemm(h, GEMM_OP_T, transA, N, K, M, 1.0f, dC, lddc, A, lda, 0.0f, dB, lddb,
+                          mode, s);
+        if (st != GEMM_OK) return st;
+        total += h->last_launches;
+    }
+    h->last_launches = total;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_profile_enable(gemm_handle_t h, int enable) {
+    if (!h) return fail_arg(h, 1);
+    h->profiling = enable != 0;
+    h->ev_used = 0;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_profile_read(gemm_handle_t h, double* main_ms, int* main_launches) {
+    if (!h) return fail_arg(h, 1);
+    if (!main_ms) return fail_arg(h, 2);
+    if (!main_launches) return fail_arg(h, 3);
+    double total = 0.0;
+    int n = 0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        if (cudaEventSynchronize(h->ev_pool[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return GEMM_ERR_CUDA;
+        }
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return GEMM_ERR_CUDA;
+        }
+        total += ms;
+        ++n;
+    }
+    h->ev_used = 0;
+    *main_ms = total;
+    *main_launches = n;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_sync(gemm_handle_t h, void* stream) {
+    if (!h) return fail_arg(h, 1);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_CUDA;
+    }
+    int word = 0;
+    if (cudaMemcpy(&word, h->err_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GEMM_ERR_CUDA;
+    if (word != 0) {
+        cudaMemset(h->err_word, 0, sizeof(int));
+        return GEMM_ERR_TIMEOUT;
+    }
+    return GEMM_OK;
+}
+
+int gemm_last_error_arg(gemm_handle_t h) { return h ? h->last_err_arg : 1; }
+
+int gemm_last_launch_count(gemm_handle_t h) { return h ? h->last_launches : 0; }
+
+const char* gemm_status_string(gemm_status_t s) {
+    switch (s) {
+        case GEMM_OK: return "GEMM_OK";
+        case GEMM_ERR_ARG: return "GEMM_ERR_ARG: invalid argument";
+        case GEMM_ERR_ALIGN: return "GEMM_ERR_ALIGN: operand not 16-byte aligned";
+        case GEMM_ERR_WORKSPACE: return "GEMM_ERR_WORKSPACE: workspace too small or allocation failed";
+        case GEMM_ERR_CUDA: return "GEMM_ERR_CUDA: CUDA call failed";
+        case GEMM_ERR_TIMEOUT: return "GEMM_ERR_TIMEOUT: a kernel's bounded wait expired";
+        case GEMM_ERR_UNSUPPORTED: return "GEMM_ERR_UNSUPPORTED: not supported by this build";
+        case GEMM_ERR_DEVICE: return "GEMM_ERR_DEVICE: current device is not sm_103";
+    }
+    return "unknown gemm_status_t";
+}
+
+}  // extern "C"

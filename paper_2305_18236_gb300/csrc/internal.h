@@ -1,0 +1,65 @@
+// Host-side interfaces between the C-ABI layer (api.cu) and the kernel
+// launchers (simt_f32.cu, split.cu, tc_gemm.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gb300 {
+
+// Tensor-core GEMM launch parameters chosen by the host.
+struct TcLaunch {
+    int bn = 256;            // tile width (tile height is 128)
+    int bk = 32;             // K depth per pipeline stage
+    int stages = 0;          // 0 = deepest ring that fits
+    int raster_group = 16;   // M tiles walked together
+    int max_ctas = 0;        // 0 = one per SM
+    int split_k = 1;         // K slices (>1: partial sums + reduce kernel)
+    long long poll_limit = 0;  // 0 = default
+};
+
+// One operand of the tensor-core kernel: BF16, K-contiguous rows,
+// `planes` stacked planes (1: hi only; 2: hi then lo), `rows` x `k`
+// elements per plane, row stride `ld` elements, plane stride `plane_ld`
+// elements.
+struct TcOperand {
+    const uint16_t* base;
+    int64_t rows;
+    int64_t k;
+    int64_t ld;
+    int64_t plane_ld;
+    int planes;
+};
+
+// C <- alpha * A_op B_op^T + beta * C where A_op is M x K and B_op is N x K
+// (both K-contiguous BF16); nterms = 1 (hi.hi) or 3 (lo.hi + hi.lo + hi.hi).
+// `partial` (split_k > 1) is split_k * M * N floats of workspace.
+// Returns 0 or a negative gemm_status_t value.
+int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M, int64_t N,
+                   int64_t K, float alpha, float beta, float* C, int64_t ldc, float* partial,
+                   const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
+                   int* launches);
+
+// FP32 SIMT GEMM (row-major, op by trans flags).
+cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                            const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                            float* C, int64_t ldc, cudaStream_t stream);
+
+// Y = op(X) split into hi/lo BF16 (lo may be null), rows x cols, row stride ldo.
+cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                              uint16_t* hi, uint16_t* lo, int64_t ldo, cudaStream_t stream);
+
+// Y = op(X) for BF16 X (a pure re-layout), rows x cols, row stride ldo.
+cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,
+                             int64_t ldx, uint16_t* out, int64_t ldo, cudaStream_t stream);
+
+// C <- beta * C (C <- 0 when beta == 0, without reading C).
+cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t ldc,
+                           cudaStream_t stream);
+
+// C <- alpha * sum_s P[s] + beta * C over split_k dense M x N slabs.
+cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int split_k, const float* P, float alpha,
+                                 float beta, float* C, int64_t ldc, cudaStream_t stream);
+
+}  // namespace gb300

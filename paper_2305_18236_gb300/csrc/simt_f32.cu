@@ -1,0 +1,215 @@
+// FP32 SIMT GEMM: C <- alpha * op(A) op(B) + beta * C on the CUDA cores.
+//
+// The "generic lowering" of Kuzma et al. (Section 3.2: llvm.matrix.multiply
+// lowered to plain vector fused multiply-adds when no matrix engine is
+// used), laid out for an SM instead of a CPU core:
+//  * a 128 x 128 C block per CTA plays the mc x nc block of Algorithm 1 and
+//    a BK = 16 slice of K plays kc;
+//  * the shared-memory tiles As[k][m], Bs[k][n] are the packed ATile/BTile
+//    buffers (Section 3.1: tiles stored in the order the micro kernel reads
+//    them), double-buffered with a register prefetch of the next K slice;
+//  * each thread's 8 x 8 register accumulator is the mr x nr micro tile of
+//    Algorithm 2, updated by rank-1 outer products and never spilled;
+//  * remainder tiles are zero-filled on load and stored element by element
+//    (Section 3.1, last paragraph), full tiles with 16-byte accesses.
+// All four op(A)/op(B) combinations are handled by the load index math.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace gb300 {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16, PAD = 4, THREADS = 256;
+
+struct Frag {
+    float v[8];
+};
+
+// Load this thread's 8 elements of the K slice [k0, k0+BK) of op(X), where
+// op(X) is R x K (R = M for A, N for B).  TRANS_K: X is stored R x K (K
+// contiguous, "K-major"); otherwise X is stored K x R (R contiguous).
+template <bool K_CONTIG, bool VEC>
+__device__ __forceinline__ void load_slice(const float* __restrict__ X, int64_t ldx, int R, int K,
+                                           int r0, int k0, bool full, Frag& f) {
+    const int t = threadIdx.x;
+    if (K_CONTIG) {
+        // thread -> row r0 + (t & 127), k0 + (t >> 7) * 8 .. +7
+        const int r = r0 + (t & 127);
+        const int k = k0 + (t >> 7) * 8;
+        const float* p = X + int64_t(r) * ldx + k;
+        if (VEC && full) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+            f.v[0] = a.x; f.v[1] = a.y; f.v[2] = a.z; f.v[3] = a.w;
+            f.v[4] = b.x; f.v[5] = b.y; f.v[6] = b.z; f.v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) f.v[q] = (r < R && k + q < K) ? __ldg(p + q) : 0.0f;
+        }
+    } else {
+        // thread -> k0 + (t >> 4), rows r0 + (t & 15) * 8 .. +7
+        const int k = k0 + (t >> 4);
+        const int r = r0 + (t & 15) * 8;
+        const float* p = X + int64_t(k) * ldx + r;
+        if (VEC && full) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+            f.v[0] = a.x; f.v[1] = a.y; f.v[2] = a.z; f.v[3] = a.w;
+            f.v[4] = b.x; f.v[5] = b.y; f.v[6] = b.z; f.v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) f.v[q] = (k < K && r + q < R) ? __ldg(p + q) : 0.0f;
+        }
+    }
+}
+
+// Store the thread's 8 elements into the [BK][BM + PAD] tile (k-major rows).
+template <bool K_CONTIG>
+__device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const Frag& f) {
+    const int t = threadIdx.x;
+    if (K_CONTIG) {
+        const int r = t & 127, k = (t >> 7) * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) S[k + q][r] = f.v[q];
+    } else {
+        const int k = t >> 4, r = (t & 15) * 8;
+        *reinterpret_cast<float4*>(&S[k][r]) = make_float4(f.v[0], f.v[1], f.v[2], f.v[3]);
+        *reinterpret_cast<float4*>(&S[k][r + 4]) = make_float4(f.v[4], f.v[5], f.v[6], f.v[7]);
+    }
+}
+
+template <bool TA, bool TB, bool VEC>
+__global__ void __launch_bounds__(THREADS, 2)
+    simt_f32_kernel(int M, int N, int K, float alpha, const float* __restrict__ A, int64_t lda,
+                    const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C,
+                    int64_t ldc, int c_vec) {
+    // op(A) rows are K-contiguous when A is stored M x K (no transpose);
+    // op(B)^T rows (N x K) are K-contiguous when B is stored N x K (transposed).
+    constexpr bool A_KC = !TA;
+    constexpr bool B_KC = TB;
+    __shared__ __align__(16) float As[2][BK][BM + PAD];
+    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
+
+    const int m0 = blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const bool mn_full = (m0 + BM <= M) && (n0 + BN <= N);
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+    const int nk = (K + BK - 1) / BK;
+    Frag fa, fb;
+    load_slice<A_KC, VEC>(A, lda, M, K, m0, 0, mn_full && BK <= K, fa);
+    load_slice<B_KC, VEC>(B, ldb, N, K, n0, 0, mn_full && BK <= K, fb);
+    store_slice<A_KC>(As[0], fa);
+    store_slice<B_KC>(Bs[0], fb);
+    __syncthreads();
+
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) {
+            const int k0 = (kt + 1) * BK;
+            const bool full = mn_full && (k0 + BK <= K);
+            load_slice<A_KC, VEC>(A, lda, M, K, m0, k0, full, fa);
+            load_slice<B_KC, VEC>(B, ldb, N, K, n0, k0, full, fb);
+        }
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) {
+            store_slice<A_KC>(As[cur ^ 1], fa);
+            store_slice<B_KC>(Bs[cur ^ 1], fb);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: C = alpha * acc + beta * C (C not read when beta == 0)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (row >= M) continue;
+        float* crow = C + int64_t(row) * ldc;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = n0 + (h == 0 ? tx * 4 : 64 + tx * 4);
+            float o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o[j] = alpha * acc[i][h * 4 + j];
+            if (c_vec && col + 4 <= N) {
+                float4* p = reinterpret_cast<float4*>(crow + col);
+                if (beta != 0.0f) {
+                    const float4 old = *p;
+                    o[0] = fmaf(beta, old.x, o[0]);
+                    o[1] = fmaf(beta, old.y, o[1]);
+                    o[2] = fmaf(beta, old.z, o[2]);
+                    o[3] = fmaf(beta, old.w, o[3]);
+                }
+                *p = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (col + j < N) {
+                        float v = o[j];
+                        if (beta != 0.0f) v = fmaf(beta, crow[col + j], v);
+                        crow[col + j] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <bool TA, bool TB>
+cudaError_t launch_tt(int M, int N, int K, float alpha, const float* A, int64_t lda,
+                      const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                      cudaStream_t stream) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (lda % 4 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(B) & 15) == 0) && (ldb % 4 == 0);
+    const int c_vec = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    if (vec)
+        simt_f32_kernel<TA, TB, true><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda, B, ldb,
+                                                                    beta, C, ldc, c_vec);
+    else
+        simt_f32_kernel<TA, TB, false><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda, B,
+                                                                     ldb, beta, C, ldc, c_vec);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                            const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                            float* C, int64_t ldc, cudaStream_t stream) {
+    if ((M + BM - 1) / BM > 65535 || M > (1ll << 31) - BM || N > (1ll << 31) - BN ||
+        K > (1ll << 31) - BK)
+        return cudaErrorInvalidValue;
+    const int m = int(M), n = int(N), k = int(K);
+    if (transA) {
+        return transB ? launch_tt<true, true>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream)
+                      : launch_tt<true, false>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+    }
+    return transB ? launch_tt<false, true>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream)
+                  : launch_tt<false, false>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+}
+
+}  // namespace gb300

@@ -1,0 +1,261 @@
+// HBM-bound helper kernels of the GEMM path.
+//
+//  * split_bf16: the packing step (Algorithm 1's pack(), Section 3.1) for the
+//    tensor-core modes: op(X) is re-laid out K-contiguous for the MMA and
+//    each FP32 value x is written as hi = bf16_rne(x), lo = bf16_rne(x - hi)
+//    (lo = 0 where hi is not finite).  x - hi is exact in FP32, so hi + lo
+//    keeps x to within 2^-16 |x|.  The split is not in the paper.
+//  * pack_bf16: the same re-layout for BF16 inputs (no arithmetic).
+//  * scale_c: C <- beta * C, the K == 0 / alpha == 0 quick return.
+//  * splitk_reduce: C <- alpha * sum_s P_s + beta * C over split-K partial
+//    sums, in increasing s (beta applied once, as in Algorithm 1).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace gb300 {
+
+namespace {
+
+__device__ __forceinline__ void split1(float x, uint16_t& h, uint16_t& l) {
+    const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+    const float hv = __bfloat162float(hb);
+    h = __bfloat16_as_ushort(hb);
+    l = isfinite(hv) ? __bfloat16_as_ushort(__float2bfloat16_rn(x - hv)) : uint16_t(0);
+}
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
+    return uint32_t(a) | (uint32_t(b) << 16);
+}
+
+int grid_for(int64_t work, int per_block) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (work + per_block - 1) / per_block;
+    return int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 16)));
+}
+
+// Y = X (no transpose): each thread converts 8 consecutive elements of a row
+// and writes 16 bytes of hi and 16 bytes of lo.
+__global__ void __launch_bounds__(256) split_rows_kernel(int64_t rows, int64_t cols,
+                                                         const float* __restrict__ X, int64_t ldx,
+                                                         uint16_t* __restrict__ hi,
+                                                         uint16_t* __restrict__ lo, int64_t ldo,
+                                                         int x_vec) {
+    const int64_t chunks_per_row = (cols + 7) / 8;
+    const int64_t total = rows * chunks_per_row;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = idx / chunks_per_row;
+        const int64_t c0 = (idx - r * chunks_per_row) * 8;
+        const float* src = X + r * ldx + c0;
+        float v[8];
+        if (x_vec && c0 + 8 <= cols) {
+            const float4 a = __ldcs(reinterpret_cast<const float4*>(src));
+            const float4 b = __ldcs(reinterpret_cast<const float4*>(src) + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = (c0 + q < cols) ? src[q] : 0.0f;
+        }
+        uint16_t h[8], l[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) split1(v[q], h[q], l[q]);
+        uint16_t* dh = hi + r * ldo + c0;
+        uint16_t* dl = lo ? lo + r * ldo + c0 : nullptr;
+        if (c0 + 8 <= cols) {
+            *reinterpret_cast<uint4*>(dh) =
+                make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+            if (dl)
+                *reinterpret_cast<uint4*>(dl) = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]),
+                                                           pack2(l[4], l[5]), pack2(l[6], l[7]));
+        } else {
+            for (int q = 0; q < 8 && c0 + q < cols; ++q) {
+                dh[q] = h[q];
+                if (dl) dl[q] = l[q];
+            }
+        }
+    }
+}
+
+// Y = X^T through a 64 x 64 shared-memory tile: reads along X's rows, writes
+// along Y's rows, both coalesced.  T is float (split into hi/lo) or
+// uint16_t (BF16 copy into `hi`).
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t cols,
+                                                        const T* __restrict__ X, int64_t ldx,
+                                                        uint16_t* __restrict__ hi,
+                                                        uint16_t* __restrict__ lo, int64_t ldo) {
+    // Y is rows x cols; X is cols x rows.  Tile: Y rows [r0, r0+64), Y cols [c0, c0+64).
+    __shared__ T tile[64][65];
+    const int64_t tiles_r = (rows + 63) / 64;
+    const int64_t tiles_c = (cols + 63) / 64;
+    const int tid = threadIdx.x;
+    for (int64_t tIdx = blockIdx.x; tIdx < tiles_r * tiles_c; tIdx += gridDim.x) {
+        const int64_t r0 = (tIdx % tiles_r) * 64;
+        const int64_t c0 = (tIdx / tiles_r) * 64;
+        // load: X row (c0 + i), columns r0 .. r0+63
+#pragma unroll
+        for (int pass = 0; pass < 16; ++pass) {
+            const int i = pass * 4 + (tid >> 6);
+            const int j = tid & 63;
+            const int64_t xr = c0 + i, xc = r0 + j;
+            tile[i][j] = (xr < cols && xc < rows) ? X[xr * ldx + xc] : T(0);
+        }
+        __syncthreads();
+        // store: Y row (r0 + rr), 8 consecutive columns per thread
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            const int rr = pass * 32 + (tid >> 3);
+            const int cc = (tid & 7) * 8;
+            const int64_t yr = r0 + rr, yc = c0 + cc;
+            if (yr < rows && yc < cols) {
+                uint16_t h[8], l[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if constexpr (sizeof(T) == 4) {
+                        split1(tile[cc + q][rr], h[q], l[q]);
+                    } else {
+                        h[q] = tile[cc + q][rr];
+                        l[q] = 0;
+                    }
+                }
+                uint16_t* dh = hi + yr * ldo + yc;
+                uint16_t* dl = lo ? lo + yr * ldo + yc : nullptr;
+                if (yc + 8 <= cols) {
+                    *reinterpret_cast<uint4*>(dh) = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]),
+                                                               pack2(h[4], h[5]), pack2(h[6], h[7]));
+                    if (dl)
+                        *reinterpret_cast<uint4*>(dl) =
+                            make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]),
+                                       pack2(l[6], l[7]));
+                } else {
+                    for (int q = 0; q < 8 && yc + q < cols; ++q) {
+                        dh[q] = h[q];
+                        if (dl) dl[q] = l[q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int64_t cols,
+                                                        const uint16_t* __restrict__ X, int64_t ldx,
+                                                        uint16_t* __restrict__ out, int64_t ldo) {
+    const int64_t total = rows * cols;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = idx / cols, c = idx - r * cols;
+        out[r * ldo + c] = X[r * ldx + c];
+    }
+}
+
+__global__ void __launch_bounds__(256) scale_c_kernel(int64_t M, int64_t N, float beta, float* C,
+                                                      int64_t ldc) {
+    const int64_t total = M * N;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = idx / N, j = idx - i * N;
+        float* c = C + i * ldc + j;
+        *c = beta == 0.0f ? 0.0f : beta * *c;
+    }
+}
+
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N, int split,
+                                                            const float* __restrict__ P,
+                                                            float alpha, float beta, float* C,
+                                                            int64_t ldc, int vec) {
+    const int64_t slab = M * N;
+    if (vec) {
+        const int64_t total = slab / 4;
+        for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+             idx += int64_t(gridDim.x) * blockDim.x) {
+            const int64_t e = idx * 4;
+            const int64_t i = e / N, j = e - i * N;
+            float4 s = __ldcs(reinterpret_cast<const float4*>(P + e));
+            for (int q = 1; q < split; ++q) {
+                const float4 t = __ldcs(reinterpret_cast<const float4*>(P + q * slab + e));
+                s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+            }
+            float4* c = reinterpret_cast<float4*>(C + i * ldc + j);
+            float4 o = make_float4(alpha * s.x, alpha * s.y, alpha * s.z, alpha * s.w);
+            if (beta != 0.0f) {
+                const float4 old = *c;
+                o.x = fmaf(beta, old.x, o.x);
+                o.y = fmaf(beta, old.y, o.y);
+                o.z = fmaf(beta, old.z, o.z);
+                o.w = fmaf(beta, old.w, o.w);
+            }
+            *c = o;
+        }
+    } else {
+        for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < slab;
+             e += int64_t(gridDim.x) * blockDim.x) {
+            const int64_t i = e / N, j = e - i * N;
+            float s = P[e];
+            for (int q = 1; q < split; ++q) s += P[q * slab + e];
+            float* c = C + i * ldc + j;
+            float o = alpha * s;
+            if (beta != 0.0f) o = fmaf(beta, *c, o);
+            *c = o;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                              uint16_t* hi, uint16_t* lo, int64_t ldo, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (!trans) {
+        const int x_vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 4 == 0);
+        const int64_t work = rows * ((cols + 7) / 8);
+        split_rows_kernel<<<grid_for(work, 256), 256, 0, stream>>>(rows, cols, X, ldx, hi, lo, ldo,
+                                                                   x_vec);
+    } else {
+        const int64_t tiles = ((rows + 63) / 64) * ((cols + 63) / 64);
+        transpose_kernel<float><<<grid_for(tiles, 1), 256, 0, stream>>>(rows, cols, X, ldx, hi, lo,
+                                                                        ldo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,
+                             int64_t ldx, uint16_t* out, int64_t ldo, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (!trans) {
+        pack_rows_kernel<<<grid_for(rows * cols, 256), 256, 0, stream>>>(rows, cols, X, ldx, out,
+                                                                          ldo);
+    } else {
+        const int64_t tiles = ((rows + 63) / 64) * ((cols + 63) / 64);
+        transpose_kernel<uint16_t><<<grid_for(tiles, 1), 256, 0, stream>>>(rows, cols, X, ldx, out,
+                                                                           nullptr, ldo);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t ldc,
+                           cudaStream_t stream) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    scale_c_kernel<<<grid_for(M * N, 256), 256, 0, stream>>>(M, N, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int split_k, const float* P, float alpha,
+                                 float beta, float* C, int64_t ldc, cudaStream_t stream) {
+    const int vec = (N % 4 == 0) && (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
+    splitk_reduce_kernel<<<grid_for(vec ? M * N / 4 : M * N, 256), 256, 0, stream>>>(
+        M, N, split_k, P, alpha, beta, C, ldc, vec);
+    return cudaGetLastError();
+}
+
+}  // namespace gb300

@@ -1,0 +1,427 @@
+// Tensor-core GEMM for sm_103a: TMA -> shared-memory ring -> tcgen05.mma
+// into tensor memory -> alpha/beta epilogue.
+//
+// This is the GPU form of Algorithm 1 (Kuzma et al., Section 3):
+//  * the paper's pack() calls (Algorithm 1, packing of A and B blocks into
+//    tile order, Section 3.1) become TMA tensor loads that drop swizzled
+//    BM x BK and BN x BK tiles into a multi-stage shared-memory ring;
+//  * the j/i block loops become a persistent tile scheduler: each CTA walks
+//    output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... in an order
+//    that keeps `raster_group` M tiles per B panel together (the paper's
+//    "pack B once, reuse it over all i");
+//  * the kk loop of llvm.matrix.multiply calls (Algorithm 2: outer-product
+//    MACs into accumulators that never spill, hardware constraint 5) becomes
+//    tcgen05.mma issued by one thread into a TMEM accumulator that lives for
+//    the whole K loop;
+//  * the alpha/beta update of the C tile (Algorithm 1, beta once, alpha on
+//    the product) is the epilogue, which reads TMEM with tcgen05.ld.
+//
+// Split-precision (nterms == 3, not in the paper): every stage holds the hi
+// and lo planes of both operands and each 16-deep K slice issues
+// acc += Alo*Bhi; acc += Ahi*Blo; acc += Ahi*Bhi (small terms first).
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
+// MMA issuer, warps 2-5 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// Two accumulators (2 x BN TMEM columns) let the epilogue of tile i overlap
+// the MMAs of tile i+1.  Every wait is bounded (ptx.cuh); on expiry the
+// kernel records the error, drains its own copies and MMAs, frees TMEM and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gb300 {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kThreads = 192;
+constexpr int kMaxSmem = 232448;  // 227 KB opt-in dynamic shared memory per block
+
+struct TcParams {
+    int M, N, K;
+    float alpha, beta;
+    float* C;
+    long long ldc;
+    int c_vec;  // C base 16-byte aligned and ldc % 4 == 0
+    int num_m, num_n, num_tiles, k_blocks;
+    int split_k, kb_per_split;
+    float* partial;  // split_k > 1: split_k slabs of M x N
+    int stages;
+    int raster_group;
+    WaitLimit lim;
+    int* err;
+};
+
+template <int BN, int BK, int NTERMS>
+struct Shape {
+    static constexpr int PLANES = NTERMS == 1 ? 1 : 2;
+    static constexpr int A_PLANE = kBM * BK * 2;
+    static constexpr int B_PLANE = BN * BK * 2;
+    static constexpr int STAGE = PLANES * (A_PLANE + B_PLANE);
+    static constexpr int TMEM_COLS = 2 * BN;  // two FP32 accumulators
+    static constexpr int ROW_BYTES = BK * 2;  // 64 (SW64) or 128 (SW128)
+    static constexpr int BAR_BYTES = 1024;    // barriers + TMEM slot + abort flag
+    static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "BK must be 32 or 64");
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
+    static int smem_bytes(int stages) { return 1024 + stages * STAGE + BAR_BYTES; }
+    static int max_stages() {
+        int s = (kMaxSmem - 1024 - BAR_BYTES) / STAGE;
+        return s > 8 ? 8 : s;
+    }
+};
+
+// Output tile t -> (m tile, n tile, k split): groups of `g` M tiles are
+// walked N-tile by N-tile, so concurrently running CTAs share B panels.
+__device__ __forceinline__ void tile_coords(int t, const TcParams& p, int& mt, int& nt, int& ks) {
+    const int per_split = p.num_m * p.num_n;
+    ks = t / per_split;
+    t -= ks * per_split;
+    const int group = p.raster_group * p.num_n;
+    const int first_m = (t / group) * p.raster_group;
+    const int gm = min(p.num_m - first_m, p.raster_group);
+    const int r = t % group;
+    mt = first_m + r % gm;
+    nt = r / gm;
+}
+
+template <int BN, int BK, int NTERMS>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcParams p) {
+    using S = Shape<BN, BK, NTERMS>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~uintptr_t(1023));
+    const int stages = p.stages;
+    uint8_t* bar_area = smem + stages * S::STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);
+    uint64_t* empty = full + stages;
+    uint64_t* acc_full = empty + stages;  // [2]
+    uint64_t* acc_empty = acc_full + 2;   // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, S::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            const uint64_t pol = l2_policy_evict_last();
+            uint32_t filled = 0;      // bit s: slot s received a fill
+            uint32_t fill_par = 0;    // bit s: parity of slot s's latest fill
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                int mt, nt, ks;
+                tile_coords(t, p, mt, nt, ks);
+                const int kb0 = ks * p.kb_per_split;
+                const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * S::STAGE;
+                    mbar_arrive_expect_tx(&full[s], S::STAGE);
+                    tma_load_3d(st, &tmA, &full[s], kb * BK, mt * kBM, 0, pol);
+                    tma_load_3d(st + S::PLANES * S::A_PLANE, &tmB, &full[s], kb * BK, nt * BN, 0,
+                                pol);
+                    filled |= 1u << s;
+                    fill_par = (fill_par & ~(1u << s)) | (ph << s);
+                }
+            }
+            // Wait for every copy this thread started before the CTA may exit.
+            for (int s = 0; s < stages; ++s)
+                if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc_bf16_f32(kBM, BN);
+            int it = 0, local = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++local) {
+                int mt, nt, ks;
+                tile_coords(t, p, mt, nt, ks);
+                const int kb0 = ks * p.kb_per_split;
+                const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
+                const int acc = local & 1;
+                const uint32_t acc_ph = (local >> 1) & 1;
+                if (!mbar_wait_bounded(&acc_empty[acc], acc_ph ^ 1, p.lim, abort_flag, p.err)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + acc * BN;
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
+                    const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the row
+                        const uint32_t first = (kb > kb0 || kk > 0) ? 1u : 0u;
+                        if (NTERMS == 3) {
+                            const uint32_t a_lo = a_hi + S::A_PLANE;
+                            const uint32_t b_lo = b_hi + S::B_PLANE;
+                            umma_bf16(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
+                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, first);
+                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                      make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc, 1u);
+                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, 1u);
+                        } else {
+                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, first);
+                        }
+                    }
+                    umma_commit(&empty[s]);  // slot free once these MMAs have read it
+                }
+                if (!ok) break;
+                umma_commit(&acc_full[acc]);  // accumulator ready for the epilogue
+            }
+            // All MMAs this thread issued must finish before TMEM is freed.
+            umma_commit(drain);
+            mbar_wait_drain(drain, 0, p.err);
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int ew = warp & 3;  // TMEM lane quarter this warp may access
+        const int row_in_tile = ew * 32 + lane;
+        int local = 0;
+        for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++local) {
+            int mt, nt, ks;
+            tile_coords(t, p, mt, nt, ks);
+            const int acc = local & 1;
+            const uint32_t acc_ph = (local >> 1) & 1;
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait_bounded(&acc_full[acc], acc_ph, p.lim, abort_flag, p.err);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int row = mt * kBM + row_in_tile;
+            const uint32_t t_row = tmem_base + (uint32_t(ew * 32) << 16) + acc * BN;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(t_row + c * 32, r);
+                tmem_ld_wait();
+                const int col0 = nt * BN + c * 32;
+                if (row < p.M && col0 < p.N) {
+                    if (p.split_k > 1) {
+                        float* dst = p.partial + (size_t(ks) * p.M + row) * size_t(p.N) + col0;
+                        if ((p.N & 3) == 0 && col0 + 32 <= p.N) {
+#pragma unroll
+                            for (int v = 0; v < 8; ++v)
+                                reinterpret_cast<float4*>(dst)[v] =
+                                    make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (col0 + j < p.N) dst[j] = __uint_as_float(r[j]);
+                        }
+                    } else {
+                        float* dst = p.C + size_t(row) * size_t(p.ldc) + col0;
+                        if (p.c_vec && col0 + 32 <= p.N) {
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) {
+                                float4 o;
+                                o.x = p.alpha * __uint_as_float(r[4 * v]);
+                                o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
+                                o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
+                                o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
+                                if (p.beta != 0.0f) {
+                                    const float4 old = reinterpret_cast<const float4*>(dst)[v];
+                                    o.x = fmaf(p.beta, old.x, o.x);
+                                    o.y = fmaf(p.beta, old.y, o.y);
+                                    o.z = fmaf(p.beta, old.z, o.z);
+                                    o.w = fmaf(p.beta, old.w, o.w);
+                                }
+                                reinterpret_cast<float4*>(dst)[v] = o;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (col0 + j < p.N) {
+                                    float o = p.alpha * __uint_as_float(r[j]);
+                                    if (p.beta != 0.0f) o = fmaf(p.beta, dst[j], o);
+                                    dst[j] = o;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
+    }
+
+    // ------------------------------------------------ teardown
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, S::TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 3-D map over (k, row, plane) of a BF16 operand, box (bk, box_rows, planes),
+// 64- or 128-byte swizzle matching the K-major UMMA descriptor.
+bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {cuuint64_t(op.k), cuuint64_t(op.rows), cuuint64_t(op.planes)};
+    cuuint64_t strides[2] = {cuuint64_t(op.ld) * 2,
+                             cuuint64_t(op.planes > 1 ? op.plane_ld : op.ld * op.rows) * 2};
+    cuuint32_t box[3] = {cuuint32_t(bk), cuuint32_t(box_rows), cuuint32_t(op.planes)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(op.base), dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    bk * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, int BK, int NTERMS>
+int launch_variant(const TcOperand& a, const TcOperand& b, TcParams p, const TcLaunch& cfg,
+                   int num_sms, cudaStream_t stream) {
+    using S = Shape<BN, BK, NTERMS>;
+    CUtensorMap ta, tb;
+    if (!encode_operand(&ta, a, BK, kBM) || !encode_operand(&tb, b, BK, BN)) return -4;
+    int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
+    if (stages < 2) stages = 2;
+    p.stages = stages;
+    // Ask for enough shared memory that co-resident CTAs can never want more
+    // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
+    const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
+    const int smem = std::max(S::smem_bytes(stages), min_smem);
+    auto kern = tc_gemm_kernel<BN, BK, NTERMS>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -4;
+    int ctas = num_sms;
+    if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
+    ctas = std::min(ctas, p.num_tiles);
+    if (ctas < 1) ctas = 1;
+    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, p);
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+}  // namespace
+
+int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M, int64_t N,
+                   int64_t K, float alpha, float beta, float* C, int64_t ldc, float* partial,
+                   const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
+                   int* launches) {
+    if (M > (1ll << 31) - 256 || N > (1ll << 31) - 256 || K > (1ll << 31) - 256) return -6;
+    const int bn = cfg.bn == 128 ? 128 : 256;
+    const int bk = cfg.bk == 64 ? 64 : 32;
+    TcParams p{};
+    p.M = int(M);
+    p.N = int(N);
+    p.K = int(K);
+    p.alpha = alpha;
+    p.beta = beta;
+    p.C = C;
+    p.ldc = ldc;
+    p.c_vec = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
+    p.num_m = int((M + kBM - 1) / kBM);
+    p.num_n = int((N + bn - 1) / bn);
+    p.k_blocks = int((K + bk - 1) / bk);
+    int split = std::max(1, cfg.split_k);
+    split = std::min(split, p.k_blocks);
+    p.kb_per_split = (p.k_blocks + split - 1) / split;
+    split = (p.k_blocks + p.kb_per_split - 1) / p.kb_per_split;  // every slice non-empty
+    p.split_k = split;
+    p.partial = partial;
+    if (split > 1 && partial == nullptr) return -3;
+    p.num_tiles = p.num_m * p.num_n * split;
+    p.raster_group = cfg.raster_group > 0 ? cfg.raster_group : 16;
+    p.lim.polls = cfg.poll_limit > 0 ? cfg.poll_limit : (1ll << 30);
+    p.lim.ns = 4000000000ull;
+    p.err = err_word;
+    int rc;
+    if (nterms == 3) {
+        if (bn == 256)
+            rc = bk == 64 ? launch_variant<256, 64, 3>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<256, 32, 3>(a, b, p, cfg, num_sms, stream);
+        else
+            rc = bk == 64 ? launch_variant<128, 64, 3>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<128, 32, 3>(a, b, p, cfg, num_sms, stream);
+    } else {
+        if (bn == 256)
+            rc = bk == 64 ? launch_variant<256, 64, 1>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<256, 32, 1>(a, b, p, cfg, num_sms, stream);
+        else
+            rc = bk == 64 ? launch_variant<128, 64, 1>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<128, 32, 1>(a, b, p, cfg, num_sms, stream);
+    }
+    if (rc != 0) return rc;
+    int n = 1;
+    if (split > 1) {
+        if (launch_splitk_reduce(M, N, split, partial, alpha, beta, C, ldc, stream) != cudaSuccess)
+            return -4;
+        ++n;
+    }
+    if (launches) *launches += n;
+    return 0;
+}
+
+}  // namespace gb300

@@ -1,0 +1,196 @@
+"""GPU parity: every mode of gemm() through the C ABI against the FP64
+oracle, element by element, on seeded inputs (GB300 only)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_18236_gb300 import inputs
+from tests.gpu_util import MODES, check_mode, make_problem, run_mode
+
+pytestmark = pytest.mark.gpu
+TRANS = [(False, False), (False, True), (True, False), (True, True)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_18236_gb300 import build
+
+    build.build()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_golden_listing1_exact(mode):
+    """The 8x5 . 5x16 tile of Listing 1 with integer data: bit-exact."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "listing1_8x5x16.json")))
+    A = np.array(g["A"], np.float32)
+    B = np.array(g["B"], np.float32)
+    C0 = np.array(g["C0"], np.float32)
+    C = run_mode(mode, A, B, g["alpha"], g["beta"], C0, False, False)
+    assert np.array_equal(C.astype(np.float64), np.array(g["C"]))
+
+
+def test_config1_simt_256():
+    """Plain SGEMM C = A B, M = N = K = 256, U[-1, 1], FP32 SIMT."""
+    A, B, _ = make_problem(256, 256, 256, dist="uniform", seed=0x5EED)
+    check_mode("f32_simt", A, B, 1.0, 0.0, None, False, False)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("tA,tB", TRANS)
+def test_transposes_ragged(mode, tA, tB):
+    """All op(A)/op(B) combinations on a shape that spans several tiles in
+    every dimension and ends in a ragged tail."""
+    M, N, K = 300, 530, 200
+    A, B, C0 = make_problem(M, N, K, tA, tB, seed=3, beta=0.5)
+    check_mode(mode, A, B, 1.5, 0.5, C0, tA, tB)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("dist", ["uniform", "log_uniform"])
+def test_distributions(mode, dist):
+    M, N, K = 384, 512, 320
+    A, B, C0 = make_problem(M, N, K, seed=5, dist=dist, beta=0.5)
+    check_mode(mode, A, B, 1.5, 0.5, C0, False, False)
+
+
+EDGE = [1, 7, 33, 127, 129, 255]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("M,N,K", [(m, n, k) for m in EDGE for n in (1, 129, 255) for k in (1, 33, 255)][::3])
+def test_edge_sizes(mode, M, N, K):
+    """Remainder handling (Section 3.1: zero-filled partial tiles, partial
+    stores) around the tile sizes."""
+    A, B, C0 = make_problem(M, N, K, seed=M * 7 + N * 3 + K, beta=0.5)
+    check_mode(mode, A, B, 1.5, 0.5, C0, False, False)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("tA,tB", TRANS)
+def test_integer_inputs_bit_exact(mode, tA, tB):
+    """Integer data in [-8, 8], K <= 4096: every partial sum is an integer
+    below 2**24, so any summation order is exact and the result must match
+    the oracle bit for bit (BF16 holds these integers exactly, so lo = 0)."""
+    M, N, K = 272, 400, 1000
+    A = inputs.integers((K, M) if tA else (M, K), 11)
+    B = inputs.integers((N, K) if tB else (K, N), 12)
+    C0 = inputs.integers((M, N), 13)
+    C = run_mode(mode, A, B, 1.5, 0.5, C0, tA, tB)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
+    assert np.array_equal(C.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_identity_and_permutation(mode):
+    """A I = A and P A = row permutation of A, exactly (A BF16-representable
+    for the BF16 mode)."""
+    X, _ = inputs.bf16_values(inputs.uniform((150, 96), 21))
+    I = np.eye(96, dtype=np.float32)
+    C = run_mode(mode, X, I, 1.0, 0.0, None, False, False)
+    assert np.array_equal(C, X)
+    perm = np.random.default_rng(3).permutation(150)
+    P = np.eye(150, dtype=np.float32)[perm]
+    C = run_mode(mode, P, X, 1.0, 0.0, None, False, False)
+    assert np.array_equal(C, X[perm])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_all_ones_closed_form(mode):
+    M, N, K = 200, 300, 777
+    C0 = inputs.integers((M, N), 4)
+    C = run_mode(mode, np.ones((M, K), np.float32), np.ones((K, N), np.float32), 1.5, 0.5, C0,
+                 False, False)
+    assert np.array_equal(C.astype(np.float64), 1.5 * K + 0.5 * C0.astype(np.float64))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_alpha_beta_special(mode):
+    """beta == 0 with NaN in C (C never read); alpha == 0 (C = beta C);
+    K == 0 (C = beta C)."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    A, B, _ = make_problem(130, 140, 150, seed=8)
+    C = torch.full((130, 140), float("nan"), device="cuda")
+    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, beta=0.0, mode=mode)
+    assert torch.isfinite(C).all()
+    C0 = inputs.uniform((130, 140), 9)
+    Cd = torch.from_numpy(C0).cuda()
+    nanA = torch.full((130, 150), float("nan"), device="cuda")
+    g.matmul(nanA, torch.from_numpy(B).cuda(), C=Cd, alpha=0.0, beta=0.5, mode=mode)
+    assert np.array_equal(Cd.cpu().numpy(), (np.float32(0.5) * C0))
+    Cd = torch.from_numpy(C0).cuda()
+    g.matmul(torch.empty((130, 0), device="cuda"), torch.empty((0, 140), device="cuda"), C=Cd,
+             alpha=1.0, beta=0.25, mode=mode)
+    assert np.array_equal(Cd.cpu().numpy(), (np.float32(0.25) * C0))
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_strided_ld(mode):
+    """Row strides larger than the row length, unaligned for 16-byte
+    vectors (ld = cols + 3), on A, B and C."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 190, 210, 170
+    A, B, C0 = make_problem(M, N, K, seed=31, beta=0.5)
+    Ab = torch.zeros((M, K + 3)); Ab[:, :K] = torch.from_numpy(A)
+    Bb = torch.zeros((K, N + 5)); Bb[:, :N] = torch.from_numpy(B)
+    Cb = torch.zeros((M, N + 3)); Cb[:, :N] = torch.from_numpy(C0)
+    Ab, Bb, Cb = Ab.cuda(), Bb.cuda(), Cb.cuda()
+    g.matmul(Ab[:, :K], Bb[:, :N], C=Cb[:, :N], alpha=1.5, beta=0.5, mode=mode)
+    torch.cuda.synchronize()
+    C64, D, _ = oracle.gemm(A, B, 1.5, 0.5, C0)
+    T64 = oracle.gemm_split_terms(A, B, 1 if mode == "bf16" else 7, 1.5, 0.5, C0)
+    out = Cb[:, :N].cpu().numpy()
+    assert oracle.normwise_error(out, T64, D) <= 1e-6
+    assert np.all(Cb[:, N:].cpu().numpy() == 0)  # padding untouched
+
+
+@pytest.mark.parametrize("split", [2, 3, 7])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_forced_split_k_exact(mode, split):
+    """Split-K (partial sums reduced in a fixed order, beta applied once --
+    Algorithm 1) is exact on integer data."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(split_k=split)
+    M, N, K = 200, 260, 1200
+    A = inputs.integers((M, K), 41)
+    B = inputs.integers((K, N), 42)
+    C0 = inputs.integers((M, N), 43)
+    C = run_mode(mode, A, B, 1.5, 0.5, C0, False, False, h=h)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0)
+    assert np.array_equal(C.astype(np.float64), ref)
+    h.close()
+
+
+@pytest.mark.parametrize("bn,bk", [(128, 32), (128, 64), (256, 32), (256, 64)])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_tile_configs(mode, bn, bk):
+    """Every compiled tile shape gives the oracle's answer."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(bn=bn, bk=bk)
+    A, B, C0 = make_problem(333, 600, 416, seed=51, beta=0.5)
+    check_mode(mode, A, B, 1.5, 0.5, C0, False, False, h=h)
+    h.close()
+
+
+def test_persistent_small_grid():
+    """Few persistent CTAs walking many tiles (accumulator double-buffer
+    and ring phases wrap many times)."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(max_ctas=3, stages=2)
+    A, B, C0 = make_problem(640, 1100, 300, seed=61, beta=0.5)
+    check_mode("bf16x3", A, B, 1.5, 0.5, C0, False, False, h=h)
+    h.close()

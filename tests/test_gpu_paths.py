@@ -1,0 +1,213 @@
+"""GPU parity of the other entry points: the split step, native BF16
+inputs, host buffers, the backward pass, argument errors, the bounded-wait
+error path, and the benchmark sizes on sampled rows (GB300 only)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_18236_gb300 import inputs
+from tests.gpu_util import check_mode, make_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_18236_gb300 import build
+
+    build.build()
+
+
+def _bits(t):
+    import torch
+
+    return t.contiguous().view(torch.int16).cpu().numpy().view(np.uint16)
+
+
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("shape", [(1, 1), (7, 9), (130, 257), (64, 64), (300, 1001)])
+def test_split_bit_exact(trans, shape):
+    """hi/lo of the split kernel equal the oracle's split bit for bit,
+    including ties, denormals, huge and non-finite values."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    X = inputs.log_uniform(shape, 71, -140.0, 128.0)
+    flat = X.reshape(-1)
+    specials = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028235e38, 1.0000153, 1e-45],
+                        np.float32)
+    flat[: min(len(specials), flat.size)] = specials[: flat.size]
+    hi, lo = g.split_bf16(torch.from_numpy(X).cuda(), trans=trans)
+    torch.cuda.synchronize()
+    Y = X.T if trans else X
+    ohi, olo = oracle.split_bf16(np.ascontiguousarray(Y))
+    ghi, glo = _bits(hi), _bits(lo)
+    nan = np.isnan(oracle.bf16_bits_to_f32(ohi))
+    assert np.array_equal(np.isnan(oracle.bf16_bits_to_f32(ghi)), nan)
+    assert np.array_equal(ghi[~nan], ohi[~nan])
+    assert np.array_equal(glo[~nan], olo[~nan])
+
+
+@pytest.mark.parametrize("tA,tB", [(False, False), (False, True), (True, False), (True, True)])
+def test_native_bf16_inputs(tA, tB):
+    """gemm_bf16 (BF16 A, B; FP32 C): products of BF16 values are exact,
+    so the only error is FP32 accumulation."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 260, 390, 300
+    A32, _ = inputs.bf16_values(inputs.normal((K, M) if tA else (M, K), 81, 1 / np.sqrt(K)))
+    B32, _ = inputs.bf16_values(inputs.normal((N, K) if tB else (K, N), 82, 1 / np.sqrt(K)))
+    C0 = inputs.uniform((M, N), 83)
+    A = torch.from_numpy(A32).cuda().to(torch.bfloat16)
+    B = torch.from_numpy(B32).cuda().to(torch.bfloat16)
+    C = torch.from_numpy(C0).cuda()
+    g.matmul_bf16(A, B, C=C, alpha=1.5, beta=0.5, transA=tA, transB=tB)
+    torch.cuda.synchronize()
+    C64, D, _ = oracle.gemm(A32, B32, 1.5, 0.5, C0, transA=tA, transB=tB)
+    assert oracle.normwise_error(C.cpu().numpy(), C64, D) <= 1e-6
+
+
+def test_native_bf16_misaligned_ld_rejected():
+    """A K-contiguous BF16 operand is read in place by TMA: an ld that is not
+    a multiple of 8 elements is GEMM_ERR_ALIGN, not a silent fallback."""
+    import torch
+
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    A = torch.zeros((64, 70), dtype=torch.bfloat16, device="cuda")[:, :67]
+    B = torch.zeros((48, 67), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(_lib.GemmError) as e:
+        g.matmul_bf16(A, B, transB=True)
+    assert e.value.status == _lib.GEMM_ERR_ALIGN
+
+
+@pytest.mark.parametrize("mode", ["f32_simt", "bf16x3"])
+def test_from_host(mode):
+    """gemm_from_host: host buffers in, host C out (pinned memory)."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    A, B, C0 = make_problem(200, 300, 250, seed=91, beta=0.5)
+    tA = torch.from_numpy(A).pin_memory()
+    tB = torch.from_numpy(B).pin_memory()
+    tC = torch.from_numpy(C0.copy()).pin_memory()
+    g.gemm_from_host(tA, tB, C=tC, alpha=1.5, beta=0.5, mode=mode)
+    C64, D, _ = oracle.gemm(A, B, 1.5, 0.5, C0)
+    tol = 1e-6 if mode == "f32_simt" else 5e-5
+    assert oracle.normwise_error(tC.numpy(), C64, D) <= tol
+
+
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, True), (False, True), (True, False)])
+def test_backward_matches_oracle_gradient(tA, tB):
+    """dA = dC op(B)^T and dB = op(A)^T dC, against the oracle's FP64 GEMMs
+    of the same closed forms."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 96, 80, 112
+    A, B, _ = make_problem(M, N, K, tA, tB, seed=101, dist="normal")
+    dC = inputs.normal((M, N), 103, 1 / np.sqrt(N))
+    dA, dB = g.gemm_backward(torch.from_numpy(dC).cuda(), torch.from_numpy(A).cuda(),
+                             torch.from_numpy(B).cuda(), transA=tA, transB=tB, mode="bf16x3")
+    torch.cuda.synchronize()
+    opB = B.T if tB else B
+    opA = A.T if tA else A
+    dA_op, DA, _ = oracle.gemm(dC, np.ascontiguousarray(opB), transB=True)  # M x K
+    dB_op, DB, _ = oracle.gemm(np.ascontiguousarray(opA), dC, transA=True)  # K x N
+    gA = dA.cpu().numpy()
+    gB = dB.cpu().numpy()
+    assert oracle.normwise_error(gA.T if tA else gA, dA_op, DA) <= 5e-5
+    assert oracle.normwise_error(gB.T if tB else gB, dB_op, DB) <= 5e-5
+
+
+def test_argument_errors_report_position():
+    """BLAS-style checks: each invalid argument returns GEMM_ERR_ARG with its
+    1-based position and launches nothing."""
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    lib = h.lib
+    p = ctypes.c_void_p(16)  # never dereferenced: every call below fails its checks first
+    base = [h.h, 0, 0, 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 2, None]
+    cases = {2: (1, 5), 3: (2, 7), 4: (3, -1), 5: (4, -1), 6: (5, -1), 8: (7, None),
+             9: (8, 7), 10: (9, None), 11: (10, 7), 13: (12, None), 14: (13, 7), 15: (14, 9)}
+    for pos, (idx, val) in cases.items():
+        args = list(base)
+        args[idx] = val
+        st = lib.gemm(*args)
+        assert st == _lib.GEMM_ERR_ARG, pos
+        assert lib.gemm_last_error_arg(h.h) == pos
+    # transposed storage changes which ld bound applies
+    args = list(base)
+    args[1], args[4], args[8] = 1, 20, 8  # A stored K x M = 8 x 20 needs lda >= 20
+    assert lib.gemm(*args) == _lib.GEMM_ERR_ARG and lib.gemm_last_error_arg(h.h) == 9
+    h.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A poll limit of one makes the tensor-core kernel's first wait on data
+    still in flight expire: the kernel drains its own copies, frees tensor
+    memory and exits; gemm_sync reports GEMM_ERR_TIMEOUT and the next call
+    on the same context is correct."""
+    import torch
+
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(wait_poll_limit=1)
+    A, B, _ = make_problem(1024, 1024, 4096, seed=111)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.zeros((1024, 1024), device="cuda")
+    g.matmul(dA, dB, C=C, mode="bf16x3", h=h)
+    assert h.sync() == _lib.GEMM_ERR_TIMEOUT
+    assert h.sync() == _lib.GEMM_OK  # the word was cleared
+    h.reset_config()
+    g.matmul(dA, dB, C=C, mode="bf16x3", h=h)
+    assert h.sync() == _lib.GEMM_OK
+    C64, D, _ = oracle.gemm(A, B, rows=np.arange(0, 1024, 97))
+    assert oracle.normwise_error(C.cpu().numpy()[::97], C64, D) <= 5e-5
+    h.close()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "log_uniform"])
+@pytest.mark.parametrize("mode", ["f32_simt", "bf16", "bf16x3"])
+def test_headline_size_sampled(mode, dist):
+    """M = N = K = 8192, alpha = 1.5, beta = 0.5, the benchmark's launch
+    configuration: 16 sampled rows checked against the oracle; the 3xBF16
+    path must reach the 1e-6 normwise bar at this size."""
+    n = 8192
+    A, B, C0 = make_problem(n, n, n, seed=0x5EED, dist=dist, beta=0.5)
+    rows = np.linspace(0, n - 1, 16).astype(np.int64)
+    tol = {"f32_simt": 1e-6, "bf16": 1e-2, "bf16x3": 1e-6}[mode]
+    check_mode(mode, A, B, 1.5, 0.5, C0, False, False, rows=rows, tol_exact=tol)
+
+
+@pytest.mark.parametrize("M,N,K", [(16384, 4096, 1024), (4096, 16384, 4096), (128, 8192, 8192),
+                                   (8192, 8192, 64)])
+def test_rectangular_bf16_sampled(M, N, K):
+    """The rectangular/skinny BF16-input shapes (normal(0, 1/sqrt(K))),
+    through gemm_bf16, on sampled rows; the skinny (128, 8192, 8192) takes
+    the split-K path."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    A32, _ = inputs.bf16_values(inputs.normal((M, K), 121, 1 / np.sqrt(K)))
+    B32, _ = inputs.bf16_values(inputs.normal((K, N), 122, 1 / np.sqrt(K)))
+    A = torch.from_numpy(A32).cuda().to(torch.bfloat16)
+    B = torch.from_numpy(B32).cuda().to(torch.bfloat16)
+    C = g.matmul_bf16(A, B)
+    torch.cuda.synchronize()
+    rows = np.linspace(0, M - 1, 12).astype(np.int64)
+    C64, D, _ = oracle.gemm(A32, B32, rows=rows)
+    assert oracle.normwise_error(C.cpu().numpy()[rows], C64, D) <= 1e-6
