@@ -79,6 +79,10 @@ typedef struct gemm_context *gemm_handle_t;
  *  split_k:   number of K slices reduced by a second kernel (1 = none).
  *  raster_group: number of M tiles walked together before moving along N.
  *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).
+ *  promote_k: GEMM_MODE_BF16X3 only: K elements summed in tensor memory
+ *    before the partial sum is added into FP32 registers with round-to-
+ *    nearest (0 = default 256, -1 = never; the tensor core's own FP32
+ *    accumulation rounds toward zero, so long chains lose accuracy).
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
  *    the device error word and exits cleanly (0 = default, about seconds). */
 typedef struct {
@@ -88,6 +92,8 @@ typedef struct {
     int32_t split_k;
     int32_t raster_group;
     int32_t max_ctas;
+    int32_t promote_k;
+    int32_t reserved; /* must be 0 */
     int64_t wait_poll_limit;
 } gemm_config_t;
 

@@ -42,7 +42,8 @@ namespace gb300 {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;               // warps 2..9
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in dynamic shared memory per block
 
 struct TcParams {
@@ -53,6 +54,7 @@ struct TcParams {
     int c_vec;  // C base 16-byte aligned and ldc % 4 == 0
     int num_m, num_n, num_tiles, k_blocks;
     int split_k, kb_per_split;
+    int chunk_kb;    // k-blocks per accumulation chunk (PROMOTE)
     float* partial;  // split_k > 1: split_k slabs of M x N
     int stages;
     int raster_group;
@@ -69,12 +71,13 @@ struct Shape {
     static constexpr int TMEM_COLS = 2 * BN;  // two FP32 accumulators
     static constexpr int ROW_BYTES = BK * 2;  // 64 (SW64) or 128 (SW128)
     static constexpr int BAR_BYTES = 1024;    // barriers + TMEM slot + abort flag
+    static constexpr int STAGING = kEpiWarps * 32 * 33 * 4;  // epilogue store slabs
     static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "BK must be 32 or 64");
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "BN");
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation is a power of two");
-    static int smem_bytes(int stages) { return 1024 + stages * STAGE + BAR_BYTES; }
+    static int smem_bytes(int stages) { return 1024 + stages * STAGE + BAR_BYTES + STAGING; }
     static int max_stages() {
-        int s = (kMaxSmem - 1024 - BAR_BYTES) / STAGE;
+        int s = (kMaxSmem - 1024 - BAR_BYTES - STAGING) / STAGE;
         return s > 8 ? 8 : s;
     }
 };
@@ -93,7 +96,51 @@ __device__ __forceinline__ void tile_coords(int t, const TcParams& p, int& mt, i
     nt = r / gm;
 }
 
-template <int BN, int BK, int NTERMS>
+// Store a 32 x 32 piece of the tile: lane l holds v[0..31] = row (row0 + l),
+// columns col0 .. col0+31.  The piece goes through this warp's padded
+// shared-memory slab so that the global accesses are coalesced: in step rr
+// the warp writes row (row0 + rr), 32 consecutive columns, one per lane.
+// Split-K stores raw FP32 partial sums; otherwise C = alpha*v + beta*C
+// (C not read when beta == 0).
+__device__ __forceinline__ void store_piece(const float* v, float* stg, int row0, int col0,
+                                            const TcParams& p, int ks, int lane) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+    __syncwarp();
+    const int col = col0 + lane;
+    if (col < p.N) {
+        if (p.split_k > 1) {
+            float* base = p.partial + size_t(ks) * p.M * size_t(p.N) + col;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = row0 + rr;
+                if (row < p.M) base[size_t(row) * p.N] = stg[rr * 33 + lane];
+            }
+        } else {
+            float* base = p.C + col;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = row0 + rr;
+                if (row < p.M) {
+                    float* dst = base + size_t(row) * size_t(p.ldc);
+                    float o = p.alpha * stg[rr * 33 + lane];
+                    if (p.beta != 0.0f) o = fmaf(p.beta, *dst, o);
+                    *dst = o;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// PROMOTE: the K range of a tile is cut into chunks of p.chunk_kb k-blocks;
+// each chunk is accumulated in TMEM from zero and then added, in FP32 with
+// round-to-nearest, into registers of the epilogue warps.  The tensor
+// core's own FP32 accumulation rounds toward zero, so its error grows with
+// the number of MMAs summed into one accumulator; short chunks bound that
+// growth and the register sums carry the rest of K with ordinary FP32
+// rounding.  Without PROMOTE a tile is one chunk.
+template <int BN, int BK, int NTERMS, bool PROMOTE>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p) {
@@ -110,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = acc_empty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* staging = reinterpret_cast<float*>(bar_area + S::BAR_BYTES);  // [kEpiWarps][32][33]
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -121,7 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
-            mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+            mbar_init(&acc_empty[a], kEpiWarps);  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -175,50 +223,57 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc_bf16_f32(kBM, BN);
-            int it = 0, local = 0;
+            int it = 0, g = 0;  // g: accumulation chunks started by this CTA
             bool ok = true;
-            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x, ++local) {
+            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
                 int mt, nt, ks;
                 tile_coords(t, p, mt, nt, ks);
                 const int kb0 = ks * p.kb_per_split;
                 const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
-                const int acc = local & 1;
-                const uint32_t acc_ph = (local >> 1) & 1;
-                if (!mbar_wait_bounded(&acc_empty[acc], acc_ph ^ 1, p.lim, abort_flag, p.err)) break;
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + acc * BN;
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % stages;
-                    const uint32_t ph = (it / stages) & 1;
-                    if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
+                const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
+                for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
+                    const int buf = g & 1;
+                    const uint32_t acc_ph = (g >> 1) & 1;
+                    if (!mbar_wait_bounded(&acc_empty[buf], acc_ph ^ 1, p.lim, abort_flag, p.err)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
-                    const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the row
-                        const uint32_t first = (kb > kb0 || kk > 0) ? 1u : 0u;
-                        if (NTERMS == 3) {
-                            const uint32_t a_lo = a_hi + S::A_PLANE;
-                            const uint32_t b_lo = b_hi + S::B_PLANE;
-                            umma_bf16(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
-                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, first);
-                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                      make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc, 1u);
-                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, 1u);
-                        } else {
-                            umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                      make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, first);
+                    const uint32_t d_tmem = tmem_base + buf * BN;
+                    const int c1 = min(c0 + chunk, kb1);
+                    for (int kb = c0; kb < c1; ++kb, ++it) {
+                        const int s = it % stages;
+                        const uint32_t ph = (it / stages) & 1;
+                        if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
+                        const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the row
+                            const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
+                            if (NTERMS == 3) {
+                                const uint32_t a_lo = a_hi + S::A_PLANE;
+                                const uint32_t b_lo = b_hi + S::B_PLANE;
+                                umma_bf16(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
+                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, acc);
+                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                          make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc, 1u);
+                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, 1u);
+                            } else {
+                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, acc);
+                            }
+                        }
+                        umma_commit(&empty[s]);  // slot free once these MMAs have read it
                     }
-                    umma_commit(&empty[s]);  // slot free once these MMAs have read it
+                    if (!ok) break;
+                    umma_commit(&acc_full[buf]);  // chunk ready for the epilogue
                 }
-                if (!ok) break;
-                umma_commit(&acc_full[acc]);  // accumulator ready for the epilogue
             }
             // All MMAs this thread issued must finish before TMEM is freed.
             umma_commit(drain);
@@ -226,76 +281,86 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ epilogue
-        const int ew = warp & 3;  // TMEM lane quarter this warp may access
-        const int row_in_tile = ew * 32 + lane;
-        int local = 0;
-        for (int t = blockIdx.x; t < p.num_tiles; t += gridDim.x, ++local) {
+        // Warp w reads TMEM lanes 32*(w%4)..+31 (tile rows) and one half of
+        // the tile's columns.
+        constexpr int COLS = BN / 2;     // columns per epilogue warp
+        constexpr int PIECES = COLS / 32;
+        const int ew = warp & 3;
+        const int col_base = ((warp - 2) >> 2) * COLS;
+        float* stg = staging + (warp - 2) * 32 * 33;
+        float sum[PROMOTE ? COLS : 1];
+        int g = 0;
+        bool ok = true;
+#pragma unroll 1
+        for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
             int mt, nt, ks;
             tile_coords(t, p, mt, nt, ks);
-            const int acc = local & 1;
-            const uint32_t acc_ph = (local >> 1) & 1;
-            int ok = 0;
-            if (lane == 0) ok = mbar_wait_bounded(&acc_full[acc], acc_ph, p.lim, abort_flag, p.err);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
-            const int row = mt * kBM + row_in_tile;
-            const uint32_t t_row = tmem_base + (uint32_t(ew * 32) << 16) + acc * BN;
+            const int kb0 = ks * p.kb_per_split;
+            const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
+            const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
+            const int row0 = mt * kBM + ew * 32;  // first tile row of this warp
+            const int col0 = nt * BN + col_base;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t r[32];
-                tmem_ld_32x32b_x32(t_row + c * 32, r);
-                tmem_ld_wait();
-                const int col0 = nt * BN + c * 32;
-                if (row < p.M && col0 < p.N) {
-                    if (p.split_k > 1) {
-                        float* dst = p.partial + (size_t(ks) * p.M + row) * size_t(p.N) + col0;
-                        if ((p.N & 3) == 0 && col0 + 32 <= p.N) {
+            for (int c0 = kb0; c0 < kb1; c0 += chunk, ++g) {
+                const int buf = g & 1;
+                const uint32_t acc_ph = (g >> 1) & 1;
+                int got = 0;
+                if (lane == 0)
+                    got = mbar_wait_bounded(&acc_full[buf], acc_ph, p.lim, abort_flag, p.err);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
+                if (PROMOTE) {
+                    // 16 columns per TMEM load keeps the live registers at
+                    // the running sums plus one 16-wide piece.
+                    if (c0 == kb0) {
 #pragma unroll
-                            for (int v = 0; v < 8; ++v)
-                                reinterpret_cast<float4*>(dst)[v] =
-                                    make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                                __uint_as_float(r[4 * v + 2]), __uint_as_float(r[4 * v + 3]));
-                        } else {
+                        for (int q = 0; q < 2 * PIECES; ++q) {
+                            uint32_t r[16];
+                            tmem_ld_32x32b_x16(taddr + q * 16, r);
+                            tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (col0 + j < p.N) dst[j] = __uint_as_float(r[j]);
+                            for (int j = 0; j < 16; ++j) sum[q * 16 + j] = __uint_as_float(r[j]);
                         }
                     } else {
-                        float* dst = p.C + size_t(row) * size_t(p.ldc) + col0;
-                        if (p.c_vec && col0 + 32 <= p.N) {
 #pragma unroll
-                            for (int v = 0; v < 8; ++v) {
-                                float4 o;
-                                o.x = p.alpha * __uint_as_float(r[4 * v]);
-                                o.y = p.alpha * __uint_as_float(r[4 * v + 1]);
-                                o.z = p.alpha * __uint_as_float(r[4 * v + 2]);
-                                o.w = p.alpha * __uint_as_float(r[4 * v + 3]);
-                                if (p.beta != 0.0f) {
-                                    const float4 old = reinterpret_cast<const float4*>(dst)[v];
-                                    o.x = fmaf(p.beta, old.x, o.x);
-                                    o.y = fmaf(p.beta, old.y, o.y);
-                                    o.z = fmaf(p.beta, old.z, o.z);
-                                    o.w = fmaf(p.beta, old.w, o.w);
-                                }
-                                reinterpret_cast<float4*>(dst)[v] = o;
-                            }
-                        } else {
+                        for (int q = 0; q < 2 * PIECES; ++q) {
+                            uint32_t r[16];
+                            tmem_ld_32x32b_x16(taddr + q * 16, r);
+                            tmem_ld_wait();
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                if (col0 + j < p.N) {
-                                    float o = p.alpha * __uint_as_float(r[j]);
-                                    if (p.beta != 0.0f) o = fmaf(p.beta, dst[j], o);
-                                    dst[j] = o;
-                                }
-                            }
+                            for (int j = 0; j < 16; ++j) sum[q * 16 + j] += __uint_as_float(r[j]);
                         }
                     }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[buf]);  // TMEM free before the stores
+                    if (c0 + chunk >= kb1) {
+#pragma unroll
+                        for (int q = 0; q < PIECES; ++q) {
+                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, p, ks, lane);
+                        }
+                    }
+                } else {
+#pragma unroll 1
+                    for (int q = 0; q < PIECES; ++q) {
+                        uint32_t r[32];
+                        tmem_ld_32x32b_x32(taddr + q * 32, r);
+                        tmem_ld_wait();
+                        float v[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                        store_piece(v, stg, row0, col0 + q * 32, p, ks, lane);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[acc]);
         }
     }
 
@@ -340,7 +405,7 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, int BK, int NTERMS>
+template <int BN, int BK, int NTERMS, bool PROMOTE>
 int launch_variant(const TcOperand& a, const TcOperand& b, TcParams p, const TcLaunch& cfg,
                    int num_sms, cudaStream_t stream) {
     using S = Shape<BN, BK, NTERMS>;
@@ -353,7 +418,7 @@ int launch_variant(const TcOperand& a, const TcOperand& b, TcParams p, const TcL
     // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
     const int smem = std::max(S::smem_bytes(stages), min_smem);
-    auto kern = tc_gemm_kernel<BN, BK, NTERMS>;
+    auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -4;
     int ctas = num_sms;
@@ -397,21 +462,33 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     p.lim.polls = cfg.poll_limit > 0 ? cfg.poll_limit : (1ll << 30);
     p.lim.ns = 4000000000ull;
     p.err = err_word;
+    // Chunked FP32 promotion for the split-precision mode (see the kernel).
+    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    p.chunk_kb = promote ? std::max(1, cfg.promote_k / bk) : 1;
     int rc;
     if (nterms == 3) {
-        if (bn == 256)
-            rc = bk == 64 ? launch_variant<256, 64, 3>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<256, 32, 3>(a, b, p, cfg, num_sms, stream);
-        else
-            rc = bk == 64 ? launch_variant<128, 64, 3>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<128, 32, 3>(a, b, p, cfg, num_sms, stream);
+        if (promote) {
+            if (bn == 256)
+                rc = bk == 64 ? launch_variant<256, 64, 3, true>(a, b, p, cfg, num_sms, stream)
+                              : launch_variant<256, 32, 3, true>(a, b, p, cfg, num_sms, stream);
+            else
+                rc = bk == 64 ? launch_variant<128, 64, 3, true>(a, b, p, cfg, num_sms, stream)
+                              : launch_variant<128, 32, 3, true>(a, b, p, cfg, num_sms, stream);
+        } else {
+            if (bn == 256)
+                rc = bk == 64 ? launch_variant<256, 64, 3, false>(a, b, p, cfg, num_sms, stream)
+                              : launch_variant<256, 32, 3, false>(a, b, p, cfg, num_sms, stream);
+            else
+                rc = bk == 64 ? launch_variant<128, 64, 3, false>(a, b, p, cfg, num_sms, stream)
+                              : launch_variant<128, 32, 3, false>(a, b, p, cfg, num_sms, stream);
+        }
     } else {
         if (bn == 256)
-            rc = bk == 64 ? launch_variant<256, 64, 1>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<256, 32, 1>(a, b, p, cfg, num_sms, stream);
+            rc = bk == 64 ? launch_variant<256, 64, 1, false>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<256, 32, 1, false>(a, b, p, cfg, num_sms, stream);
         else
-            rc = bk == 64 ? launch_variant<128, 64, 1>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<128, 32, 1>(a, b, p, cfg, num_sms, stream);
+            rc = bk == 64 ? launch_variant<128, 64, 1, false>(a, b, p, cfg, num_sms, stream)
+                          : launch_variant<128, 32, 1, false>(a, b, p, cfg, num_sms, stream);
     }
     if (rc != 0) return rc;
     int n = 1;

@@ -66,8 +66,9 @@ class Gemm:
 
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
-                   wait_poll_limit=0):
-        cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, wait_poll_limit)
+                   promote_k=0, wait_poll_limit=0):
+        cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, 0,
+                            wait_poll_limit)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
 
     def reset_config(self):
@@ -191,6 +192,7 @@ def gemm_from_host(A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False
     M, N, K = _dims(A, B, transA, transB)
     if C is None:
         C = torch.empty((M, N), dtype=torch.float32, pin_memory=A.is_pinned())
+    h.ensure_workspace(h.workspace_size(_mode(mode), transA, transB, M, N, K))
     s = _stream(h.device) if stream is None else ctypes.c_void_p(stream)
     st = h.lib.gemm_from_host(h.h, int(transA), int(transB), M, N, K, float(alpha),
                               ctypes.c_void_p(A.data_ptr()), _ld(A),
