@@ -218,6 +218,28 @@ gemm_status_t gemm_profile_enable(gemm_handle_t handle, int enable);
  * their number; then forget them. */
 gemm_status_t gemm_profile_read(gemm_handle_t handle, double *main_ms, int *main_launches);
 
+/* gemm() in GEMM_MODE_BF16X3 for callers that cannot allocate device
+ * memory (code running where cudaMalloc is forbidden or would stall, such as
+ * host callbacks, allocator hooks, or plugins whose host owns all device
+ * memory).  No handle: it calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The paper has no counterpart.
+ * Scratch is one 64 MiB device array inside the library, reserved on every
+ * GPU that loads the library until the process exits; a problem must fit:
+ * 4 * (M + N) * round_up(K, 8) bytes <= 64 MiB, else GEMM_ERR_WORKSPACE and
+ * nothing is launched.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture.  All calls share the array (it keeps the last
+ * call's contents; each call overwrites what it reads): calls whose GPU
+ * work overlaps, on different streams or threads, race -- serialise them.
+ * Invalid arguments give GEMM_ERR_ARG (no position is recorded: there is no
+ * handle); a bounded-wait expiry is not reported.  Same arguments and
+ * results as gemm() in GEMM_MODE_BF16X3 without split-K. */
+gemm_status_t gemm_bf16x3_noalloc(gemm_op_t transA, gemm_op_t transB,
+                                  int64_t M, int64_t N, int64_t K,
+                                  float alpha, const float *A, int64_t lda,
+                                  const float *B, int64_t ldb,
+                                  float beta, float *C, int64_t ldc, void *stream);
+
 /* Synchronise `stream`, then read and clear the handle's device error word:
  * GEMM_ERR_TIMEOUT if a kernel abandoned a bounded wait since the last
  * check, GEMM_ERR_CUDA if the stream reported an error, else GEMM_OK. */
