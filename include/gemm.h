@@ -81,7 +81,7 @@ typedef struct gemm_context *gemm_handle_t;
  *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).
  *  promote_k: GEMM_MODE_BF16X3 only: K elements summed in tensor memory
  *    before the partial sum is added into FP32 registers with round-to-
- *    nearest (0 = default 256, -1 = never; the tensor core's own FP32
+ *    nearest (0 = default 512, -1 = never; the tensor core's own FP32
  *    accumulation rounds toward zero, so long chains lose accuracy).
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
  *    the device error word and exits cleanly (0 = default, about seconds). */

@@ -62,7 +62,7 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
     c.raster_group = h->cfg.raster_group ? h->cfg.raster_group : 16;
     c.max_ctas = h->cfg.max_ctas;
     c.poll_limit = h->cfg.wait_poll_limit;
-    c.promote_k = h->cfg.promote_k == 0 ? 256 : (h->cfg.promote_k < 0 ? 0 : h->cfg.promote_k);
+    c.promote_k = h->cfg.promote_k == 0 ? 512 : (h->cfg.promote_k < 0 ? 0 : h->cfg.promote_k);
     if (h->cfg.split_k > 0) {
         c.split_k = h->cfg.split_k;
     } else {

@@ -17,7 +17,7 @@ struct TcLaunch {
     int max_ctas = 0;        // 0 = one per SM
     int split_k = 1;         // K slices (>1: partial sums + reduce kernel)
     long long poll_limit = 0;  // 0 = default
-    int promote_k = 256;     // split-precision: K elements per TMEM chunk (0 = no promotion)
+    int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
 };
 
 // One operand of the tensor-core kernel: BF16, K-contiguous rows,

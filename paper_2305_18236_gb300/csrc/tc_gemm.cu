@@ -100,37 +100,62 @@ __device__ __forceinline__ void tile_coords(int t, const TcParams& p, int& mt, i
 // columns col0 .. col0+31.  The piece goes through this warp's padded
 // shared-memory slab so that the global accesses are coalesced: in step rr
 // the warp writes row (row0 + rr), 32 consecutive columns, one per lane.
-// Split-K stores raw FP32 partial sums; otherwise C = alpha*v + beta*C
-// (C not read when beta == 0).
+// All 32 reads of C are issued before the first store so that their
+// latencies overlap.  Split-K stores raw FP32 partial sums; otherwise
+// C = alpha*v + beta*C (C not read when beta == 0).
 __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0, int col0,
                                             const TcParams& p, int ks, int lane) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
     __syncwarp();
     const int col = col0 + lane;
+    const int rows = min(32, p.M - row0);
     if (col < p.N) {
         if (p.split_k > 1) {
-            float* base = p.partial + size_t(ks) * p.M * size_t(p.N) + col;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int row = row0 + rr;
-                if (row < p.M) base[size_t(row) * p.N] = stg[rr * 33 + lane];
-            }
+            float* base = p.partial + (size_t(ks) * p.M + row0) * size_t(p.N) + col;
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr)
+                if (rr < rows) base[size_t(rr) * p.N] = stg[rr * 33 + lane];
         } else {
-            float* base = p.C + col;
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-                const int row = row0 + rr;
-                if (row < p.M) {
-                    float* dst = base + size_t(row) * size_t(p.ldc);
-                    float o = p.alpha * stg[rr * 33 + lane];
-                    if (p.beta != 0.0f) o = fmaf(p.beta, *dst, o);
-                    *dst = o;
+            float* base = p.C + size_t(row0) * size_t(p.ldc) + col;
+            const size_t ldc = size_t(p.ldc);
+            if (p.beta != 0.0f) {
+                // eight reads of C in flight per batch
+#pragma unroll
+                for (int r0 = 0; r0 < 32; r0 += 8) {
+                    float old[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        old[i] = r0 + i < rows ? base[(r0 + i) * ldc] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (r0 + i < rows)
+                            base[(r0 + i) * ldc] =
+                                fmaf(p.beta, old[i], p.alpha * stg[(r0 + i) * 33 + lane]);
                 }
+            } else {
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr)
+                    if (rr < rows) base[rr * ldc] = p.alpha * stg[rr * 33 + lane];
             }
         }
     }
     __syncwarp();
+}
+
+// Ask L2 to fetch this warp's part of the C tile (rows row0..row0+31,
+// `cols` columns from col0) ahead of the beta * C reads.
+__device__ __forceinline__ void prefetch_c(const TcParams& p, int row0, int col0, int cols,
+                                           int lane) {
+    if (p.beta == 0.0f || p.split_k > 1) return;
+    const int lines_per_row = cols / 32;  // 128-byte lines
+    for (int l = lane; l < 32 * lines_per_row; l += 32) {
+        const int rr = l / lines_per_row, c = col0 + (l % lines_per_row) * 32;
+        if (row0 + rr < p.M && c < p.N) {
+            const float* a = p.C + size_t(row0 + rr) * size_t(p.ldc) + c;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+        }
+    }
 }
 
 // PROMOTE: the K range of a tile is cut into chunks of p.chunk_kb k-blocks;
@@ -314,6 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
+                // one chunk before the final store, start pulling C into L2
+                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1) prefetch_c(p, row0, col0, COLS, lane);
                 if (PROMOTE) {
                     // 16 columns per TMEM load keeps the live registers at
                     // the running sums plus one 16-wide piece.

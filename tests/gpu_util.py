@@ -13,7 +13,7 @@ Tolerances, derived from the arithmetic of each path:
     toward zero, losing less than one ulp of the running sum (<= D) per
     MMA: at most (number of MMAs summed in one TMEM chain + 2) * 2**-23.
     bf16 sums all ceil(K/16) MMAs in one chain; bf16x3 sums chains of
-    3 * 256/16 = 48 MMAs and adds the chains in FP32 with round-to-nearest
+    3 * 512/16 = 96 MMAs and adds the chains in FP32 with round-to-nearest
     (at most 2**-24 each).
   * bf16x3 vs the exact FP64 GEMM: the three kept products miss lo*lo and
     the split residuals, each below 2**-16 |a b|: 3 * 2**-16 plus the
@@ -26,7 +26,7 @@ import torch
 import oracle
 from paper_2305_18236_gb300 import inputs
 
-PROMOTE_K = 256  # K elements per TMEM chain in the bf16x3 mode (library default)
+PROMOTE_K = 512  # K elements per TMEM chain in the bf16x3 mode (library default)
 
 
 def tol_terms(mode, K):
