@@ -184,16 +184,58 @@ typedef struct {
     int32_t transA, transB; /* gemm_op_t values */
 } gemm_problem_t;
 
-/* Many independent FP32 GEMMs in one call (split passes plus one persistent
- * tensor-core launch over all problems' tiles).  host_problems (HOST
- * memory, `count` entries) describe the problems; their pointers are
- * device pointers.  Supports GEMM_MODE_BF16 and GEMM_MODE_BF16X3.  Not in
- * the paper; the per-problem tile parameters play the role of its
- * per-target mc/kc/nc blocking (Section 3.1, Eqs. 1-7).  Positions:
- * 1 handle, 2 mode, 3 host_problems (index of the first bad problem is
- * reported as 100 + problem index), 4 count, 5 stream. */
+/* Many independent FP32 GEMMs in one call: one split launch for all
+ * operands plus one persistent tensor-core launch over the concatenated
+ * output tiles of all problems.  host_problems (HOST memory, `count`
+ * entries) describe the problems; their pointers are device pointers.
+ * GEMM_MODE_BF16 and GEMM_MODE_BF16X3 only.  Not in the paper; the launch's
+ * tile parameters play the role of its per-target mc/kc/nc blocking
+ * (Section 3.1, Eqs. 1-7).  This convenience call builds a plan, runs it and
+ * frees it, so it allocates and synchronises the device; use the plan API
+ * below for repeated calls.  Positions: 1 handle, 2 mode, 3 host_problems
+ * (a bad problem i is reported as 100 + i), 4 count, 5 stream. */
 gemm_status_t gemm_grouped(gemm_handle_t handle, gemm_mode_t mode,
                            const gemm_problem_t *host_problems, int32_t count, void *stream);
+
+typedef struct gemm_grouped_plan_s *gemm_grouped_plan_t;
+
+/* Flags of gemm_grouped_plan_create. */
+enum {
+    GEMM_GROUPED_AUTOTUNE = 1, /* choose tile shape, stage depth and raster by timing */
+    GEMM_GROUPED_GRAPH = 2     /* capture the launches in a CUDA graph and replay it */
+};
+
+/* Prepare a grouped GEMM: validate the problems, allocate the plan's device
+ * tables and BF16 split workspace (cudaMalloc; the plan owns them) and fix
+ * the launch configuration.  With GEMM_GROUPED_AUTOTUNE the configurations a
+ * shared-memory / tensor-memory feasibility model admits are ranked by a cost
+ * model (padded tile work x wave quantisation), the best few are timed on the
+ * problems themselves -- writing only to plan-owned scratch, never to any
+ * C -- and the fastest is kept; results are cached per process (and in the
+ * file named by the GEMM_AUTOTUNE_CACHE environment variable, if set) keyed
+ * by SM count, mode and problem shapes.  Tuning runs on `stream` and
+ * synchronises it.  Without it, the handle's configuration is used.  The
+ * problems' pointers and sizes are fixed at creation.  Positions: 1 handle,
+ * 2 mode, 3 host_problems (100 + i for problem i), 4 count, 5 flags,
+ * 6 stream, 7 plan. */
+gemm_status_t gemm_grouped_plan_create(gemm_handle_t handle, gemm_mode_t mode,
+                                       const gemm_problem_t *host_problems, int32_t count,
+                                       uint32_t flags, void *stream, gemm_grouped_plan_t *plan);
+
+/* Enqueue the plan on `stream`: the split launch, the tensor-core launch and
+ * one scaling launch per problem with K == 0 or alpha == 0.  With
+ * GEMM_GROUPED_GRAPH and a non-NULL stream, the first run captures these
+ * launches in a CUDA graph and every run replays that graph.  Runs of one
+ * plan share its workspace: do not let them overlap on different streams. */
+gemm_status_t gemm_grouped_plan_run(gemm_grouped_plan_t plan, void *stream);
+
+/* The configuration the plan launches with, and the tuned time of one
+ * tensor-core launch on the tuning subset in ms (0 if not tuned). */
+gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t plan, gemm_config_t *cfg,
+                                       double *tuned_ms);
+
+/* Synchronise the device and free the plan.  NULL is accepted. */
+gemm_status_t gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
 
 /* Gradients of C = op(A) op(B) (alpha = 1, beta = 0) for a given dC:
  *   dA = dC op(B)^T  (stored like A: M x K, or K x M when transA == T),

@@ -24,6 +24,8 @@ GEMM_ERR_TIMEOUT = -5
 GEMM_ERR_UNSUPPORTED = -6
 GEMM_ERR_DEVICE = -7
 
+GROUPED_AUTOTUNE, GROUPED_GRAPH = 1, 2
+
 _i32, _i64, _f32, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
 
@@ -55,6 +57,12 @@ _SIGS = {
     "gemm_from_host": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _f32,
                                       _vp, _i64, _vp, _i64, _f32, _vp, _i64, ctypes.c_int, _vp]),
     "gemm_grouped": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gemm_problem_t), _i32, _vp]),
+    "gemm_grouped_plan_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(gemm_problem_t),
+                                                _i32, ctypes.c_uint32, _vp, ctypes.POINTER(_vp)]),
+    "gemm_grouped_plan_run": (ctypes.c_int, [_vp, _vp]),
+    "gemm_grouped_plan_config": (ctypes.c_int, [_vp, ctypes.POINTER(gemm_config_t),
+                                                ctypes.POINTER(ctypes.c_double)]),
+    "gemm_grouped_plan_destroy": (ctypes.c_int, [_vp]),
     "gemm_backward": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _i64,
                                      _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_int,
                                      _vp]),

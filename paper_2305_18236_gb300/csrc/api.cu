@@ -259,6 +259,19 @@ gemm_status_t grow(float** p, size_t* have, size_t want) {
 
 }  // namespace
 
+// Accessors for the grouped-plan translation unit (grouped.cu).
+namespace gb300 {
+int handle_device(gemm_handle_t h) { return h->device; }
+int handle_num_sms(gemm_handle_t h) { return h->num_sms; }
+int* handle_err_word(gemm_handle_t h) { return h->err_word; }
+void handle_set_err_arg(gemm_handle_t h, int pos) { h->last_err_arg = pos; }
+void handle_set_launches(gemm_handle_t h, int n) { h->last_launches = n; }
+TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
+    // tile choice of the handle's configuration (problem-size independent parts)
+    return plan_tc(h, nterms, 1 << 20, 1 << 20, 1);
+}
+}  // namespace gb300
+
 extern "C" {
 
 gemm_status_t gemm_create(gemm_handle_t* handle) {
@@ -462,17 +475,6 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     st = gemm_sync(h, stream);
     h->last_launches = launches;
     return st;
-}
-
-gemm_status_t gemm_grouped(gemm_handle_t h, gemm_mode_t mode, const gemm_problem_t* host_problems,
-                           int32_t count, void* stream) {
-    (void)stream;
-    if (!h) return fail_arg(h, 1);
-    h->last_err_arg = 0;
-    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return fail_arg(h, 2);
-    if (count < 0) return fail_arg(h, 4);
-    if (count > 0 && !host_problems) return fail_arg(h, 3);
-    return GEMM_ERR_UNSUPPORTED;
 }
 
 gemm_status_t gemm_backward(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int64_t M,

@@ -1,0 +1,566 @@
+// Grouped GEMM: many independent C_g = alpha_g op(A_g) op(B_g) + beta_g C_g
+// in one split launch plus one persistent tensor-core launch.
+//
+// Not in the paper.  Its per-target blocking parameters (mc, kc, nc chosen
+// from cache sizes, Section 3.1, Eqs. 1-7) have a GPU analogue here: the
+// tile width BN, the stage depth BK and the ring depth are chosen per launch
+// by an autotuner whose analytic seed is a feasibility-and-cost model of
+// shared memory (227 KB per CTA), tensor memory (512 columns per SM) and
+// tile quantisation, refined by timing the surviving candidates on the
+// problems themselves.
+//
+// A plan owns its device tables (problem descriptors, tensor maps, split
+// jobs) and the BF16 hi/lo workspace; running it enqueues only kernels, so
+// it can be captured into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gemm.h"
+#include "internal.h"
+
+struct gemm_grouped_plan_s {
+    gemm_handle_t handle = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int* err_word = nullptr;
+    int nterms = 3;
+    uint32_t flags = 0;
+    gb300::TcLaunch cfg;
+    double tuned_ms = 0.0;
+    // device allocations owned by the plan
+    uint8_t* ws = nullptr;
+    gb300::SplitJob* d_jobs = nullptr;
+    gb300::GroupedProblem* d_probs = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    int njobs = 0, split_tiles = 0, nprobs = 0, total_tiles = 0;
+    // problems handled by a plain scale (K == 0 or alpha == 0)
+    struct Scale {
+        int64_t M, N, ldc;
+        float beta;
+        float* C;
+    };
+    std::vector<Scale> scales;
+    // graph replay
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t exec_stream = nullptr;
+    int launches = 0;
+};
+
+namespace {
+
+using gb300::GroupedProblem;
+using gb300::SplitJob;
+using gb300::TcLaunch;
+using gb300::TcOperand;
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// One tensor-core problem of the plan, host side.
+struct HostProb {
+    TcOperand a, b;
+    int64_t M, N, K, ldc;
+    float alpha, beta;
+    float* C;
+};
+
+// Problem table and tensor maps for a tile shape; returns total tiles.
+int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
+                 std::vector<GroupedProblem>& probs, std::vector<CUtensorMap>& maps,
+                 bool* ok) {
+    probs.clear();
+    maps.assign(2 * ps.size(), CUtensorMap{});
+    int tiles = 0;
+    *ok = true;
+    for (size_t i = 0; i < ps.size(); ++i) {
+        const HostProb& q = ps[i];
+        GroupedProblem g{};
+        g.C = q.C;
+        g.ldc = q.ldc;
+        g.M = int(q.M);
+        g.N = int(q.N);
+        g.K = int(q.K);
+        g.num_m = int((q.M + 127) / 128);
+        g.num_n = int((q.N + bn - 1) / bn);
+        g.k_blocks = int((q.K + bk - 1) / bk);
+        g.tile_start = tiles;
+        g.alpha = q.alpha;
+        g.beta = q.beta;
+        tiles += g.num_m * g.num_n;
+        probs.push_back(g);
+        if (!gb300::encode_operand(&maps[2 * i], q.a, bk, 128) ||
+            !gb300::encode_operand(&maps[2 * i + 1], q.b, bk, bn))
+            *ok = false;
+    }
+    (void)nterms;
+    return tiles;
+}
+
+// Analytic seed: which (BN, BK) exist on this SM and what they should cost.
+// Cost = padded tensor work of every tile (tiles are 128 x BN, so ragged
+// edges waste work) times the wave-quantisation factor of the persistent
+// grid, times a penalty for rings shallower than four stages.
+struct Candidate {
+    TcLaunch cfg;
+    double model;
+};
+
+std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nterms, int num_sms,
+                                       const TcLaunch& base) {
+    std::vector<Candidate> out;
+    const int kmax_smem = 232448;
+    for (int bn : {256, 128}) {
+        for (int bk : {32, 64}) {
+            int stages = 0;
+            for (int s = 8; s >= 2; --s)
+                if (gb300::tc_smem_bytes(nterms, bn, bk, s) <= kmax_smem) {
+                    stages = s;
+                    break;
+                }
+            if (stages < 2 || 2 * bn > 512) continue;  // shared memory or TMEM does not fit
+            double work = 0.0, tiles = 0.0;
+            for (const HostProb& q : ps) {
+                const double nm = double((q.M + 127) / 128), nn = double((q.N + bn - 1) / bn);
+                const double kk = double((q.K + bk - 1) / bk) * bk;
+                work += nm * nn * 128.0 * bn * kk;
+                tiles += nm * nn;
+            }
+            const double waves = std::ceil(tiles / num_sms) / (tiles / num_sms);
+            const double shallow = stages < 4 ? 1.15 : 1.0;
+            // 128 x 128 tiles read A twice per output element: extra operand traffic
+            const double narrow = bn == 128 ? 1.10 : 1.0;
+            Candidate c;
+            c.cfg = base;
+            c.cfg.bn = bn;
+            c.cfg.bk = bk;
+            c.cfg.stages = stages;
+            c.cfg.split_k = 1;
+            c.model = work * waves * shallow * narrow;
+            out.push_back(c);
+        }
+    }
+    std::sort(out.begin(), out.end(),
+              [](const Candidate& x, const Candidate& y) { return x.model < y.model; });
+    return out;
+}
+
+std::string shape_key(int device_sms, int nterms, const std::vector<HostProb>& ps) {
+    // order-independent signature: count and a hash of the sorted shapes
+    std::vector<uint64_t> v;
+    for (const HostProb& q : ps)
+        v.push_back((uint64_t(q.M) << 42) ^ (uint64_t(q.N) << 21) ^ uint64_t(q.K));
+    std::sort(v.begin(), v.end());
+    uint64_t h = 1469598103934665603ull;
+    for (uint64_t x : v) {
+        h ^= x;
+        h *= 1099511628211ull;
+    }
+    char buf[96];
+    snprintf(buf, sizeof buf, "sms%d-t%d-n%zu-%016llx", device_sms, nterms, ps.size(),
+             (unsigned long long)h);
+    return buf;
+}
+
+std::mutex g_cache_mu;
+std::map<std::string, TcLaunch> g_cache;
+
+bool cache_lookup(const std::string& key, TcLaunch* out) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        *out = it->second;
+        return true;
+    }
+    // optional persistent cache: lines "key bn bk stages raster"
+    const char* path = getenv("GEMM_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char k[128];
+    int bn, bk, st, rg;
+    bool found = false;
+    while (fscanf(f, "%127s %d %d %d %d", k, &bn, &bk, &st, &rg) == 5) {
+        if (key == k) {
+            out->bn = bn;
+            out->bk = bk;
+            out->stages = st;
+            out->raster_group = rg;
+            found = true;
+        }
+    }
+    fclose(f);
+    if (found) g_cache[key] = *out;
+    return found;
+}
+
+void cache_store(const std::string& key, const TcLaunch& c) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_cache[key] = c;
+    const char* path = getenv("GEMM_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group);
+    fclose(f);
+}
+
+template <typename T>
+gemm_status_t upload(T** dst, const std::vector<T>& v, cudaStream_t s) {
+    if (v.empty()) return GEMM_OK;
+    if (!*dst && cudaMalloc(reinterpret_cast<void**>(dst), v.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_WORKSPACE;
+    }
+    if (cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return GEMM_ERR_CUDA;
+    return GEMM_OK;
+}
+
+void free_plan(gemm_grouped_plan_s* p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->ws) cudaFree(p->ws);
+    if (p->d_jobs) cudaFree(p->d_jobs);
+    if (p->d_probs) cudaFree(p->d_probs);
+    if (p->d_maps) cudaFree(p->d_maps);
+    delete p;
+}
+
+// Time one configuration on (a subset of) the problems with C redirected to
+// plan-owned scratch and beta = 0, so the caller's C is never touched.
+double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaunch& cfg,
+                      int* err_word, int num_sms, cudaStream_t s) {
+    std::vector<GroupedProblem> probs;
+    std::vector<CUtensorMap> maps;
+    bool ok = true;
+    const int tiles = build_tables(sub, cfg.bn, cfg.bk, nterms, probs, maps, &ok);
+    if (!ok) return -1.0;
+    GroupedProblem* dp = nullptr;
+    CUtensorMap* dm = nullptr;
+    double best = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (upload(&dp, probs, s) == GEMM_OK && upload(&dm, maps, s) == GEMM_OK &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            const int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, int(sub.size()), tiles,
+                                                    err_word, num_sms, s);
+            cudaEventRecord(e1, s);
+            if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
+                best = -1.0;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && (best < 0.0 || ms < best)) best = ms;  // first launch is warm-up
+        }
+    }
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (dp) cudaFree(dp);
+    if (dm) cudaFree(dm);
+    return best;
+}
+
+gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
+    for (const auto& sc : p->scales)
+        if (gb300::launch_scale_c(sc.M, sc.N, sc.beta, sc.C, sc.ldc, s) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+    if (gb300::launch_split_grouped(p->d_jobs, p->njobs, p->split_tiles, p->num_sms, s) !=
+        cudaSuccess)
+        return GEMM_ERR_CUDA;
+    const int rc = gb300::launch_tc_grouped(p->nterms, p->cfg, p->d_probs, p->d_maps, p->nprobs,
+                                            p->total_tiles, p->err_word, p->num_sms, s);
+    return rc == 0 ? GEMM_OK : static_cast<gemm_status_t>(rc);
+}
+
+}  // namespace
+
+// Declared by api.cu's context; grouped.cu only needs these three fields.
+namespace gb300 {
+int handle_device(gemm_handle_t h);
+int handle_num_sms(gemm_handle_t h);
+int* handle_err_word(gemm_handle_t h);
+void handle_set_err_arg(gemm_handle_t h, int pos);
+void handle_set_launches(gemm_handle_t h, int n);
+TcLaunch handle_tc_config(gemm_handle_t h, int nterms);
+}  // namespace gb300
+
+extern "C" {
+
+gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
+                                       const gemm_problem_t* hp, int32_t count, uint32_t flags,
+                                       void* stream, gemm_grouped_plan_t* plan) {
+    if (!h) return GEMM_ERR_ARG;
+    gb300::handle_set_err_arg(h, 0);
+    auto bad = [&](int pos) {
+        gb300::handle_set_err_arg(h, pos);
+        return GEMM_ERR_ARG;
+    };
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return bad(2);
+    if (count < 0) return bad(4);
+    if (count > 0 && !hp) return bad(3);
+    if (flags & ~uint32_t(GEMM_GROUPED_AUTOTUNE | GEMM_GROUPED_GRAPH)) return bad(5);
+    if (!plan) return bad(7);
+    *plan = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
+    const int planes = nterms == 3 ? 2 : 1;
+
+    // validate every problem exactly as gemm() would
+    for (int i = 0; i < count; ++i) {
+        const gemm_problem_t& q = hp[i];
+        const bool ta = q.transA != 0, tb = q.transB != 0;
+        const bool reads = q.M > 0 && q.N > 0 && q.K > 0 && q.alpha != 0.0f;
+        const int64_t lim = (int64_t(1) << 31) - 1024;
+        if ((q.transA != 0 && q.transA != 1) || (q.transB != 0 && q.transB != 1) || q.M < 0 ||
+            q.N < 0 || q.K < 0 || q.M > lim || q.N > lim || q.K > lim ||
+            (reads && (!q.A || !q.B)) || q.lda < std::max<int64_t>(1, ta ? q.M : q.K) ||
+            q.ldb < std::max<int64_t>(1, tb ? q.K : q.N) || (q.M > 0 && q.N > 0 && !q.C) ||
+            q.ldc < std::max<int64_t>(1, q.N))
+            return bad(100 + i);
+    }
+
+    auto* p = new gemm_grouped_plan_s();
+    p->handle = h;
+    p->device = gb300::handle_device(h);
+    p->num_sms = gb300::handle_num_sms(h);
+    p->err_word = gb300::handle_err_word(h);
+    p->nterms = nterms;
+    p->flags = flags;
+    p->cfg = gb300::handle_tc_config(h, nterms);
+    p->cfg.split_k = 1;
+
+    // workspace layout: per problem, A planes [planes][M][Kp] then B planes [planes][N][Kp]
+    std::vector<HostProb> ps;
+    std::vector<SplitJob> jobs;
+    std::vector<size_t> a_off, b_off;
+    size_t ws = 0;
+    for (int i = 0; i < count; ++i) {
+        const gemm_problem_t& q = hp[i];
+        if (q.M == 0 || q.N == 0) continue;
+        if (q.K == 0 || q.alpha == 0.0f) {
+            p->scales.push_back({q.M, q.N, q.ldc, q.beta, q.C});
+            continue;
+        }
+        const int64_t kp = (q.K + 7) / 8 * 8;
+        a_off.push_back(ws);
+        ws += round256(size_t(planes) * q.M * kp * 2);
+        b_off.push_back(ws);
+        ws += round256(size_t(planes) * q.N * kp * 2);
+    }
+    if (ws > 0 && cudaMalloc(reinterpret_cast<void**>(&p->ws), ws) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return GEMM_ERR_WORKSPACE;
+    }
+    int tiles = 0;
+    size_t idx = 0;
+    for (int i = 0; i < count; ++i) {
+        const gemm_problem_t& q = hp[i];
+        if (q.M == 0 || q.N == 0 || q.K == 0 || q.alpha == 0.0f) continue;
+        const int64_t kp = (q.K + 7) / 8 * 8;
+        uint16_t* ah = reinterpret_cast<uint16_t*>(p->ws + a_off[idx]);
+        uint16_t* bh = reinterpret_cast<uint16_t*>(p->ws + b_off[idx]);
+        ++idx;
+        SplitJob ja{};
+        ja.src = q.A;
+        ja.ldx = q.lda;
+        ja.hi = ah;
+        ja.lo = planes > 1 ? ah + q.M * kp : nullptr;
+        ja.ldo = kp;
+        ja.rows = int(q.M);
+        ja.cols = int(q.K);
+        ja.trans = q.transA;
+        ja.x_vec = ((reinterpret_cast<uintptr_t>(q.A) & 15) == 0) && (q.lda % 4 == 0);
+        ja.tiles_r = int((q.M + 63) / 64);
+        ja.tile_start = tiles;
+        tiles += ja.tiles_r * int((q.K + 63) / 64);
+        jobs.push_back(ja);
+        SplitJob jb{};
+        jb.src = q.B;
+        jb.ldx = q.ldb;
+        jb.hi = bh;
+        jb.lo = planes > 1 ? bh + q.N * kp : nullptr;
+        jb.ldo = kp;
+        jb.rows = int(q.N);
+        jb.cols = int(q.K);
+        jb.trans = !q.transB;  // op(B)^T is N x K
+        jb.x_vec = ((reinterpret_cast<uintptr_t>(q.B) & 15) == 0) && (q.ldb % 4 == 0);
+        jb.tiles_r = int((q.N + 63) / 64);
+        jb.tile_start = tiles;
+        tiles += jb.tiles_r * int((q.K + 63) / 64);
+        jobs.push_back(jb);
+        HostProb hq;
+        hq.a = TcOperand{ah, q.M, q.K, kp, q.M * kp, planes};
+        hq.b = TcOperand{bh, q.N, q.K, kp, q.N * kp, planes};
+        hq.M = q.M;
+        hq.N = q.N;
+        hq.K = q.K;
+        hq.ldc = q.ldc;
+        hq.alpha = q.alpha;
+        hq.beta = q.beta;
+        hq.C = q.C;
+        ps.push_back(hq);
+    }
+    p->njobs = int(jobs.size());
+    p->split_tiles = tiles;
+    p->nprobs = int(ps.size());
+    gemm_status_t st = upload(&p->d_jobs, jobs, s);
+    if (st != GEMM_OK) {
+        free_plan(p);
+        return st;
+    }
+
+    if ((flags & GEMM_GROUPED_AUTOTUNE) && !ps.empty()) {
+        const std::string key = shape_key(p->num_sms, nterms, ps);
+        TcLaunch hit = p->cfg;
+        if (cache_lookup(key, &hit)) {
+            p->cfg.bn = hit.bn;
+            p->cfg.bk = hit.bk;
+            p->cfg.stages = hit.stages;
+            p->cfg.raster_group = hit.raster_group;
+        } else {
+            // operands must be split before the candidates can be timed
+            if (gb300::launch_split_grouped(p->d_jobs, p->njobs, p->split_tiles, p->num_sms, s) !=
+                cudaSuccess) {
+                free_plan(p);
+                return GEMM_ERR_CUDA;
+            }
+            // tune on the leading problems whose outputs fit in 512 MB of scratch
+            std::vector<HostProb> sub;
+            size_t cbytes = 0;
+            for (const HostProb& q : ps) {
+                const size_t b = round256(size_t(q.M) * q.N * 4);
+                if (!sub.empty() && cbytes + b > (size_t(512) << 20)) break;
+                sub.push_back(q);
+                cbytes += b;
+            }
+            uint8_t* scratch = nullptr;
+            if (cudaMalloc(reinterpret_cast<void**>(&scratch), cbytes) != cudaSuccess) {
+                cudaGetLastError();
+                free_plan(p);
+                return GEMM_ERR_WORKSPACE;
+            }
+            size_t off = 0;
+            for (HostProb& q : sub) {
+                q.C = reinterpret_cast<float*>(scratch + off);
+                q.ldc = q.N;
+                q.alpha = 1.0f;
+                q.beta = 0.0f;
+                off += round256(size_t(q.M) * q.N * 4);
+            }
+            std::vector<Candidate> cands = seed_candidates(sub, nterms, p->num_sms, p->cfg);
+            double best = -1.0;
+            TcLaunch best_cfg = p->cfg;
+            const size_t tries = std::min<size_t>(cands.size(), 4);
+            for (size_t c = 0; c < tries; ++c) {
+                for (int rg : {8, 16}) {
+                    TcLaunch cfg = cands[c].cfg;
+                    cfg.raster_group = rg;
+                    const double ms =
+                        time_candidate(sub, nterms, cfg, p->err_word, p->num_sms, s);
+                    if (ms > 0.0 && (best < 0.0 || ms < best)) {
+                        best = ms;
+                        best_cfg = cfg;
+                    }
+                }
+            }
+            cudaFree(scratch);
+            if (best > 0.0) {
+                p->cfg = best_cfg;
+                p->tuned_ms = best;
+                cache_store(key, best_cfg);
+            }
+        }
+    }
+
+    std::vector<GroupedProblem> probs;
+    std::vector<CUtensorMap> maps;
+    bool ok = true;
+    p->total_tiles = build_tables(ps, p->cfg.bn, p->cfg.bk, nterms, probs, maps, &ok);
+    if (!ok) {
+        free_plan(p);
+        return GEMM_ERR_CUDA;
+    }
+    if ((st = upload(&p->d_probs, probs, s)) != GEMM_OK || (st = upload(&p->d_maps, maps, s)) != GEMM_OK) {
+        free_plan(p);
+        return st;
+    }
+    p->launches = int(p->scales.size()) + (p->njobs > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0);
+    *plan = p;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_grouped_plan_run(gemm_grouped_plan_t p, void* stream) {
+    if (!p) return GEMM_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gb300::handle_set_launches(p->handle, p->launches);
+    if (!(p->flags & GEMM_GROUPED_GRAPH) || s == nullptr) return enqueue(p, s);
+    if (!p->exec) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        const gemm_status_t st = enqueue(p, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != GEMM_OK || ce != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return st != GEMM_OK ? st : GEMM_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&p->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            p->exec = nullptr;
+            cudaGetLastError();
+            return GEMM_ERR_CUDA;
+        }
+    }
+    return cudaGraphLaunch(p->exec, s) == cudaSuccess ? GEMM_OK : GEMM_ERR_CUDA;
+}
+
+gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg,
+                                       double* tuned_ms) {
+    if (!p) return GEMM_ERR_ARG;
+    if (cfg) {
+        *cfg = gemm_config_t{};
+        cfg->bn = p->cfg.bn;
+        cfg->bk = p->cfg.bk;
+        cfg->stages = p->cfg.stages;
+        cfg->split_k = 1;
+        cfg->raster_group = p->cfg.raster_group;
+        cfg->max_ctas = p->cfg.max_ctas;
+        cfg->promote_k = p->cfg.promote_k > 0 ? p->cfg.promote_k : -1;
+        cfg->wait_poll_limit = p->cfg.poll_limit;
+    }
+    if (tuned_ms) *tuned_ms = p->tuned_ms;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_grouped_plan_destroy(gemm_grouped_plan_t p) {
+    if (!p) return GEMM_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_grouped(gemm_handle_t h, gemm_mode_t mode, const gemm_problem_t* host_problems,
+                           int32_t count, void* stream) {
+    gemm_grouped_plan_t plan = nullptr;
+    gemm_status_t st = gemm_grouped_plan_create(h, mode, host_problems, count, 0, stream, &plan);
+    if (st != GEMM_OK) return st;
+    st = gemm_grouped_plan_run(plan, stream);
+    gemm_grouped_plan_destroy(plan);
+    return st;
+}
+
+}  // extern "C"

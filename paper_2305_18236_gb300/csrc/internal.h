@@ -33,6 +33,34 @@ struct TcOperand {
     int planes;
 };
 
+// One problem of a grouped tensor-core launch, as the kernel reads it from
+// device memory.  tile_start is the index of the problem's first output
+// tile in the launch's concatenated tile space (a prefix sum).
+struct GroupedProblem {
+    float* C;
+    long long ldc;
+    int M, N, K;
+    int num_m, num_n, k_blocks;
+    int tile_start;
+    float alpha, beta;
+    int pad;
+};
+
+// Encode the 3-D (k, row, plane) TMA map of a K-contiguous BF16 operand with
+// a (bk, box_rows, planes) box and the swizzle the UMMA descriptor expects.
+bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows);
+
+// Grouped launch: `count` problems described by dev_problems (device) with
+// two tensor maps each in dev_maps (device, encoded with cfg.bk and a box of
+// 128 rows for A and cfg.bn rows for B); total_tiles = sum of num_m * num_n.
+int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev_problems,
+                      const CUtensorMap* dev_maps, int count, int total_tiles, int* err_word,
+                      int num_sms, cudaStream_t stream);
+
+// Dynamic shared memory the tensor-core kernel asks for with this config
+// (0 if the configuration does not exist).
+int tc_smem_bytes(int nterms, int bn, int bk, int stages);
+
 // C <- alpha * A_op B_op^T + beta * C where A_op is M x K and B_op is N x K
 // (both K-contiguous BF16); nterms = 1 (hi.hi) or 3 (lo.hi + hi.lo + hi.hi).
 // `partial` (split_k > 1) is split_k * M * N floats of workspace.
@@ -50,6 +78,26 @@ cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_
 // Y = op(X) split into hi/lo BF16 (lo may be null), rows x cols, row stride ldo.
 cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float* X, int64_t ldx,
                               uint16_t* hi, uint16_t* lo, int64_t ldo, cudaStream_t stream);
+
+// One matrix of a grouped split launch (device table entry): Y = op(X),
+// rows x cols, written as hi/lo BF16 with row stride ldo; tile_start is the
+// prefix sum of 64 x 64 output tiles over the preceding jobs.
+struct SplitJob {
+    const float* src;
+    long long ldx;
+    uint16_t* hi;
+    uint16_t* lo;
+    long long ldo;
+    int rows, cols;
+    int trans;
+    int x_vec;  // src 16-byte aligned and ldx % 4 == 0
+    int tile_start;
+    int tiles_r;  // (rows + 63) / 64
+};
+
+// Split every job of the table in one launch (total_tiles 64 x 64 tiles).
+cudaError_t launch_split_grouped(const SplitJob* dev_jobs, int njobs, int total_tiles,
+                                 int num_sms, cudaStream_t stream);
 
 // Y = op(X) for BF16 X (a pure re-layout), rows x cols, row stride ldo.
 cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,

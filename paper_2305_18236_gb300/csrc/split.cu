@@ -210,7 +210,116 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N
     }
 }
 
+// Grouped split: the concatenated 64 x 64 output tiles of all jobs; each
+// block finds its job by binary search over the prefix sums.  Transposed
+// jobs go through a shared-memory tile; the others convert straight along
+// the rows (each thread 16 consecutive elements of one row).
+__global__ void __launch_bounds__(256) split_grouped_kernel(const SplitJob* __restrict__ jobs,
+                                                            int njobs, int total_tiles) {
+    __shared__ float tile[64][65];
+    const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        int lo_j = 0, hi_j = njobs - 1;
+        while (lo_j < hi_j) {
+            const int mid = (lo_j + hi_j + 1) >> 1;
+            if (__ldg(&jobs[mid].tile_start) <= t)
+                lo_j = mid;
+            else
+                hi_j = mid - 1;
+        }
+        const SplitJob& j = jobs[lo_j];
+        const int local = t - j.tile_start;
+        const int64_t r0 = int64_t(local % j.tiles_r) * 64;
+        const int64_t c0 = int64_t(local / j.tiles_r) * 64;
+        if (j.trans) {
+            // X is cols x rows: read X rows c0.., columns r0.. coalesced
+#pragma unroll
+            for (int pass = 0; pass < 16; ++pass) {
+                const int i = pass * 4 + (tid >> 6);
+                const int jj = tid & 63;
+                const int64_t xr = c0 + i, xc = r0 + jj;
+                tile[i][jj] = (xr < j.cols && xc < j.rows) ? j.src[xr * j.ldx + xc] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+                const int rr = pass * 32 + (tid >> 3);
+                const int cc = (tid & 7) * 8;
+                const int64_t yr = r0 + rr, yc = c0 + cc;
+                if (yr < j.rows && yc < j.cols) {
+                    uint16_t h[8], l[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) split1(tile[cc + q][rr], h[q], l[q]);
+                    uint16_t* dh = j.hi + yr * j.ldo + yc;
+                    uint16_t* dl = j.lo ? j.lo + yr * j.ldo + yc : nullptr;
+                    if (yc + 8 <= j.cols) {
+                        *reinterpret_cast<uint4*>(dh) = make_uint4(
+                            pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+                        if (dl)
+                            *reinterpret_cast<uint4*>(dl) =
+                                make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]),
+                                           pack2(l[6], l[7]));
+                    } else {
+                        for (int q = 0; q < 8 && yc + q < j.cols; ++q) {
+                            dh[q] = h[q];
+                            if (dl) dl[q] = l[q];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        } else {
+            const int64_t yr = r0 + (tid >> 2);
+            const int64_t yc = c0 + (tid & 3) * 16;
+            if (yr < j.rows && yc < j.cols) {
+                const float* src = j.src + yr * j.ldx + yc;
+                float v[16];
+                if (j.x_vec && yc + 16 <= j.cols) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 a = __ldcs(reinterpret_cast<const float4*>(src) + q);
+                        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = yc + q < j.cols ? src[q] : 0.0f;
+                }
+                uint16_t h[16], l[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) split1(v[q], h[q], l[q]);
+                uint16_t* dh = j.hi + yr * j.ldo + yc;
+                uint16_t* dl = j.lo ? j.lo + yr * j.ldo + yc : nullptr;
+                if (yc + 16 <= j.cols) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        reinterpret_cast<uint4*>(dh)[q] =
+                            make_uint4(pack2(h[8 * q], h[8 * q + 1]), pack2(h[8 * q + 2], h[8 * q + 3]),
+                                       pack2(h[8 * q + 4], h[8 * q + 5]), pack2(h[8 * q + 6], h[8 * q + 7]));
+                        if (dl)
+                            reinterpret_cast<uint4*>(dl)[q] = make_uint4(
+                                pack2(l[8 * q], l[8 * q + 1]), pack2(l[8 * q + 2], l[8 * q + 3]),
+                                pack2(l[8 * q + 4], l[8 * q + 5]), pack2(l[8 * q + 6], l[8 * q + 7]));
+                    }
+                } else {
+                    for (int q = 0; q < 16 && yc + q < j.cols; ++q) {
+                        dh[q] = h[q];
+                        if (dl) dl[q] = l[q];
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_grouped(const SplitJob* dev_jobs, int njobs, int total_tiles,
+                                 int num_sms, cudaStream_t stream) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    const int grid = std::max(1, std::min(total_tiles, num_sms * 8));
+    split_grouped_kernel<<<grid, 256, 0, stream>>>(dev_jobs, njobs, total_tiles);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float* X, int64_t ldx,
                               uint16_t* hi, uint16_t* lo, int64_t ldo, cudaStream_t stream) {

@@ -51,7 +51,6 @@ struct TcParams {
     float alpha, beta;
     float* C;
     long long ldc;
-    int c_vec;  // C base 16-byte aligned and ldc % 4 == 0
     int num_m, num_n, num_tiles, k_blocks;
     int split_k, kb_per_split;
     int chunk_kb;    // k-blocks per accumulation chunk (PROMOTE)
@@ -60,6 +59,11 @@ struct TcParams {
     int raster_group;
     WaitLimit lim;
     int* err;
+    // grouped launches: problem table (prefix-summed tile starts) and two
+    // tensor maps per problem (A then B), all in device memory
+    const GroupedProblem* problems;
+    const CUtensorMap* maps;
+    int count;
 };
 
 template <int BN, int BK, int NTERMS>
@@ -82,62 +86,134 @@ struct Shape {
     }
 };
 
-// Output tile t -> (m tile, n tile, k split): groups of `g` M tiles are
-// walked N-tile by N-tile, so concurrently running CTAs share B panels.
-__device__ __forceinline__ void tile_coords(int t, const TcParams& p, int& mt, int& nt, int& ks) {
-    const int per_split = p.num_m * p.num_n;
-    ks = t / per_split;
-    t -= ks * per_split;
-    const int group = p.raster_group * p.num_n;
-    const int first_m = (t / group) * p.raster_group;
-    const int gm = min(p.num_m - first_m, p.raster_group);
+// Where output tile t sits: coordinates, K-block range, operand maps.
+struct TileInfo {
+    int mt, nt, ks, kb0, kb1;
+    int prob;  // problem index (grouped launches)
+    const CUtensorMap* ma;
+    const CUtensorMap* mb;
+};
+
+// The output side of a tile's problem (looked up only where it is used, so
+// that it does not occupy registers across the K loop).
+struct EpiInfo {
+    int M, N;
+    float alpha, beta;
+    float* C;
+    long long ldc;
+};
+
+// Local tile index -> (m tile, n tile): groups of `g` M tiles are walked
+// N-tile by N-tile, so concurrently running CTAs share B panels in L2.
+__device__ __forceinline__ void raster(int t, int num_m, int num_n, int g, int& mt, int& nt) {
+    const int group = g * num_n;
+    const int first_m = (t / group) * g;
+    const int gm = min(num_m - first_m, g);
     const int r = t % group;
     mt = first_m + r % gm;
     nt = r / gm;
+}
+
+template <bool GROUPED>
+__device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUtensorMap* tmA,
+                                             const CUtensorMap* tmB) {
+    TileInfo ti;
+    if (!GROUPED) {
+        const int per_split = p.num_m * p.num_n;
+        ti.ks = t / per_split;
+        raster(t - ti.ks * per_split, p.num_m, p.num_n, p.raster_group, ti.mt, ti.nt);
+        ti.kb0 = ti.ks * p.kb_per_split;
+        ti.kb1 = min(ti.kb0 + p.kb_per_split, p.k_blocks);
+        ti.prob = 0;
+        ti.ma = tmA;
+        ti.mb = tmB;
+    } else {
+        // last problem whose first tile is <= t
+        int lo = 0, hi = p.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.problems[mid].tile_start) <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const GroupedProblem* q = p.problems + lo;
+        ti.ks = 0;
+        raster(t - __ldg(&q->tile_start), __ldg(&q->num_m), __ldg(&q->num_n), p.raster_group,
+               ti.mt, ti.nt);
+        ti.kb0 = 0;
+        ti.kb1 = __ldg(&q->k_blocks);
+        ti.prob = lo;
+        ti.ma = p.maps + 2 * lo;
+        ti.mb = p.maps + 2 * lo + 1;
+    }
+    return ti;
+}
+
+// Split-K launches write raw partial sums: their "C" is slab ks of the
+// partial buffer with alpha = 1, beta = 0.
+template <bool GROUPED>
+__device__ __forceinline__ EpiInfo get_epi(int prob, int ks, const TcParams& p) {
+    EpiInfo e;
+    if (!GROUPED) {
+        e.M = p.M;
+        e.N = p.N;
+        if (p.split_k > 1) {
+            e.alpha = 1.0f;
+            e.beta = 0.0f;
+            e.C = p.partial + size_t(ks) * size_t(p.M) * size_t(p.N);
+            e.ldc = p.N;
+        } else {
+            e.alpha = p.alpha;
+            e.beta = p.beta;
+            e.C = p.C;
+            e.ldc = p.ldc;
+        }
+    } else {
+        const GroupedProblem* q = p.problems + prob;
+        e.M = __ldg(&q->M);
+        e.N = __ldg(&q->N);
+        e.alpha = __ldg(&q->alpha);
+        e.beta = __ldg(&q->beta);
+        e.C = q->C;
+        e.ldc = __ldg(&q->ldc);
+    }
+    return e;
 }
 
 // Store a 32 x 32 piece of the tile: lane l holds v[0..31] = row (row0 + l),
 // columns col0 .. col0+31.  The piece goes through this warp's padded
 // shared-memory slab so that the global accesses are coalesced: in step rr
 // the warp writes row (row0 + rr), 32 consecutive columns, one per lane.
-// All 32 reads of C are issued before the first store so that their
-// latencies overlap.  Split-K stores raw FP32 partial sums; otherwise
-// C = alpha*v + beta*C (C not read when beta == 0).
+// Reads of C are issued eight at a time so that their latencies overlap.
+// Split-K stores raw FP32 partial sums; otherwise C = alpha*v + beta*C
+// (C not read when beta == 0).
 __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0, int col0,
-                                            const TcParams& p, int ks, int lane) {
+                                            const EpiInfo& e, int lane) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
     __syncwarp();
     const int col = col0 + lane;
-    const int rows = min(32, p.M - row0);
-    if (col < p.N) {
-        if (p.split_k > 1) {
-            float* base = p.partial + (size_t(ks) * p.M + row0) * size_t(p.N) + col;
+    const int rows = min(32, e.M - row0);
+    if (col < e.N) {
+        float* base = e.C + size_t(row0) * size_t(e.ldc) + col;
+        const size_t ldc = size_t(e.ldc);
+        if (e.beta != 0.0f) {
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += 8) {
+                float old[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) old[i] = r0 + i < rows ? base[(r0 + i) * ldc] : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (r0 + i < rows)
+                        base[(r0 + i) * ldc] =
+                            fmaf(e.beta, old[i], e.alpha * stg[(r0 + i) * 33 + lane]);
+            }
+        } else {
 #pragma unroll 8
             for (int rr = 0; rr < 32; ++rr)
-                if (rr < rows) base[size_t(rr) * p.N] = stg[rr * 33 + lane];
-        } else {
-            float* base = p.C + size_t(row0) * size_t(p.ldc) + col;
-            const size_t ldc = size_t(p.ldc);
-            if (p.beta != 0.0f) {
-                // eight reads of C in flight per batch
-#pragma unroll
-                for (int r0 = 0; r0 < 32; r0 += 8) {
-                    float old[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        old[i] = r0 + i < rows ? base[(r0 + i) * ldc] : 0.0f;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (r0 + i < rows)
-                            base[(r0 + i) * ldc] =
-                                fmaf(p.beta, old[i], p.alpha * stg[(r0 + i) * 33 + lane]);
-                }
-            } else {
-#pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr)
-                    if (rr < rows) base[rr * ldc] = p.alpha * stg[rr * 33 + lane];
-            }
+                if (rr < rows) base[rr * ldc] = e.alpha * stg[rr * 33 + lane];
         }
     }
     __syncwarp();
@@ -145,27 +221,20 @@ __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0
 
 // Ask L2 to fetch this warp's part of the C tile (rows row0..row0+31,
 // `cols` columns from col0) ahead of the beta * C reads.
-__device__ __forceinline__ void prefetch_c(const TcParams& p, int row0, int col0, int cols,
+__device__ __forceinline__ void prefetch_c(const EpiInfo& ti, int row0, int col0, int cols,
                                            int lane) {
-    if (p.beta == 0.0f || p.split_k > 1) return;
+    if (ti.beta == 0.0f) return;
     const int lines_per_row = cols / 32;  // 128-byte lines
     for (int l = lane; l < 32 * lines_per_row; l += 32) {
         const int rr = l / lines_per_row, c = col0 + (l % lines_per_row) * 32;
-        if (row0 + rr < p.M && c < p.N) {
-            const float* a = p.C + size_t(row0 + rr) * size_t(p.ldc) + c;
+        if (row0 + rr < ti.M && c < ti.N) {
+            const float* a = ti.C + size_t(row0 + rr) * size_t(ti.ldc) + c;
             asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
         }
     }
 }
 
-// PROMOTE: the K range of a tile is cut into chunks of p.chunk_kb k-blocks;
-// each chunk is accumulated in TMEM from zero and then added, in FP32 with
-// round-to-nearest, into registers of the epilogue warps.  The tensor
-// core's own FP32 accumulation rounds toward zero, so its error grows with
-// the number of MMAs summed into one accumulator; short chunks bound that
-// growth and the register sums carry the rest of K with ordinary FP32
-// rounding.  Without PROMOTE a tile is one chunk.
-template <int BN, int BK, int NTERMS, bool PROMOTE>
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcParams p) {
@@ -199,8 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
+        if (!GROUPED) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+        }
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, S::TMEM_COLS);
@@ -220,11 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-                int mt, nt, ks;
-                tile_coords(t, p, mt, nt, ks);
-                const int kb0 = ks * p.kb_per_split;
-                const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+                for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
@@ -233,9 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     uint8_t* st = smem + s * S::STAGE;
                     mbar_arrive_expect_tx(&full[s], S::STAGE);
-                    tma_load_3d(st, &tmA, &full[s], kb * BK, mt * kBM, 0, pol);
-                    tma_load_3d(st + S::PLANES * S::A_PLANE, &tmB, &full[s], kb * BK, nt * BN, 0,
-                                pol);
+                    tma_load_3d(st, ti.ma, &full[s], kb * BK, ti.mt * kBM, 0, pol);
+                    tma_load_3d(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], kb * BK, ti.nt * BN,
+                                0, pol);
                     filled |= 1u << s;
                     fill_par = (fill_par & ~(1u << s)) | (ph << s);
                 }
@@ -251,10 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0, g = 0;  // g: accumulation chunks started by this CTA
             bool ok = true;
             for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-                int mt, nt, ks;
-                tile_coords(t, p, mt, nt, ks);
-                const int kb0 = ks * p.kb_per_split;
-                const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
+                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+                const int kb0 = ti.kb0, kb1 = ti.kb1;
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                     const int buf = g & 1;
@@ -318,13 +384,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
 #pragma unroll 1
         for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-            int mt, nt, ks;
-            tile_coords(t, p, mt, nt, ks);
-            const int kb0 = ks * p.kb_per_split;
-            const int kb1 = min(kb0 + p.kb_per_split, p.k_blocks);
+            const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+            const int kb0 = ti.kb0, kb1 = ti.kb1;
             const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
-            const int row0 = mt * kBM + ew * 32;  // first tile row of this warp
-            const int col0 = nt * BN + col_base;
+            const int row0 = ti.mt * kBM + ew * 32;  // first tile row of this warp
+            const int col0 = ti.nt * BN + col_base;
 #pragma unroll 1
             for (int c0 = kb0; c0 < kb1; c0 += chunk, ++g) {
                 const int buf = g & 1;
@@ -340,7 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
                 // one chunk before the final store, start pulling C into L2
-                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1) prefetch_c(p, row0, col0, COLS, lane);
+                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1)
+                    prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0, col0, COLS, lane);
                 if (PROMOTE) {
                     // 16 columns per TMEM load keeps the live registers at
                     // the running sums plus one 16-wide piece.
@@ -367,9 +432,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);  // TMEM free before the stores
                     if (c0 + chunk >= kb1) {
+                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
 #pragma unroll
                         for (int q = 0; q < PIECES; ++q) {
-                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, p, ks, lane);
+                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
                         }
                     }
                 } else {
@@ -381,7 +447,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                        store_piece(v, stg, row0, col0 + q * 32, p, ks, lane);
+                        store_piece(v, stg, row0, col0 + q * 32,
+                                    get_epi<GROUPED>(ti.prob, ti.ks, p), lane);
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -415,8 +482,62 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over (k, row, plane) of a BF16 operand, box (bk, box_rows, planes),
-// 64- or 128-byte swizzle matching the K-major UMMA descriptor.
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
+int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p, const TcLaunch& cfg,
+                   int num_sms, cudaStream_t stream) {
+    using S = Shape<BN, BK, NTERMS>;
+    int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
+    if (stages < 2) stages = 2;
+    p.stages = stages;
+    // Ask for enough shared memory that co-resident CTAs can never want more
+    // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
+    const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
+    const int smem = std::max(S::smem_bytes(stages), min_smem);
+    auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE, GROUPED>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -4;
+    int ctas = num_sms;
+    if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
+    ctas = std::min(ctas, p.num_tiles);
+    if (ctas < 1) ctas = 1;
+    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, p);
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <bool GROUPED>
+int dispatch(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
+             const CUtensorMap& tb, const TcParams& p, const TcLaunch& cfg, int num_sms,
+             cudaStream_t s) {
+#define GB300_TC_CASE(BN_, BK_, NT_, PR_)                                                      \
+    if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
+        return launch_variant<BN_, BK_, NT_, PR_, GROUPED>(ta, tb, p, cfg, num_sms, s);
+    GB300_TC_CASE(256, 32, 3, true)
+    GB300_TC_CASE(256, 64, 3, true)
+    GB300_TC_CASE(128, 32, 3, true)
+    GB300_TC_CASE(128, 64, 3, true)
+    GB300_TC_CASE(256, 32, 3, false)
+    GB300_TC_CASE(256, 64, 3, false)
+    GB300_TC_CASE(128, 32, 3, false)
+    GB300_TC_CASE(128, 64, 3, false)
+    GB300_TC_CASE(256, 32, 1, false)
+    GB300_TC_CASE(256, 64, 1, false)
+    GB300_TC_CASE(128, 32, 1, false)
+    GB300_TC_CASE(128, 64, 1, false)
+#undef GB300_TC_CASE
+    return -6;
+}
+
+void fill_common(TcParams& p, const TcLaunch& cfg, int bk, int nterms, int* err_word) {
+    p.raster_group = cfg.raster_group > 0 ? cfg.raster_group : 16;
+    p.lim.polls = cfg.poll_limit > 0 ? cfg.poll_limit : (1ll << 30);
+    p.lim.ns = 4000000000ull;
+    p.err = err_word;
+    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    p.chunk_kb = promote ? std::max(1, cfg.promote_k / bk) : 1;
+}
+
+}  // namespace
+
 bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -432,31 +553,12 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, int BK, int NTERMS, bool PROMOTE>
-int launch_variant(const TcOperand& a, const TcOperand& b, TcParams p, const TcLaunch& cfg,
-                   int num_sms, cudaStream_t stream) {
-    using S = Shape<BN, BK, NTERMS>;
-    CUtensorMap ta, tb;
-    if (!encode_operand(&ta, a, BK, kBM) || !encode_operand(&tb, b, BK, BN)) return -4;
-    int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
-    if (stages < 2) stages = 2;
-    p.stages = stages;
-    // Ask for enough shared memory that co-resident CTAs can never want more
-    // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
-    const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
-    const int smem = std::max(S::smem_bytes(stages), min_smem);
-    auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -4;
-    int ctas = num_sms;
-    if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
-    ctas = std::min(ctas, p.num_tiles);
-    if (ctas < 1) ctas = 1;
-    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, p);
-    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+int tc_smem_bytes(int nterms, int bn, int bk, int stages) {
+    const int planes = nterms == 1 ? 1 : 2;
+    if ((bn != 128 && bn != 256) || (bk != 32 && bk != 64)) return 0;
+    const int stage = planes * (kBM * bk * 2 + bn * bk * 2);
+    return 1024 + stages * stage + 1024 + kEpiWarps * 32 * 33 * 4;
 }
-
-}  // namespace
 
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M, int64_t N,
                    int64_t K, float alpha, float beta, float* C, int64_t ldc, float* partial,
@@ -473,7 +575,6 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     p.beta = beta;
     p.C = C;
     p.ldc = ldc;
-    p.c_vec = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
     p.num_m = int((M + kBM - 1) / kBM);
     p.num_n = int((N + bn - 1) / bn);
     p.k_blocks = int((K + bk - 1) / bk);
@@ -485,38 +586,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     p.partial = partial;
     if (split > 1 && partial == nullptr) return -3;
     p.num_tiles = p.num_m * p.num_n * split;
-    p.raster_group = cfg.raster_group > 0 ? cfg.raster_group : 16;
-    p.lim.polls = cfg.poll_limit > 0 ? cfg.poll_limit : (1ll << 30);
-    p.lim.ns = 4000000000ull;
-    p.err = err_word;
-    // Chunked FP32 promotion for the split-precision mode (see the kernel).
+    fill_common(p, cfg, bk, nterms, err_word);
+    CUtensorMap ta, tb;
+    if (!encode_operand(&ta, a, bk, kBM) || !encode_operand(&tb, b, bk, bn)) return -4;
     const bool promote = nterms == 3 && cfg.promote_k > 0;
-    p.chunk_kb = promote ? std::max(1, cfg.promote_k / bk) : 1;
-    int rc;
-    if (nterms == 3) {
-        if (promote) {
-            if (bn == 256)
-                rc = bk == 64 ? launch_variant<256, 64, 3, true>(a, b, p, cfg, num_sms, stream)
-                              : launch_variant<256, 32, 3, true>(a, b, p, cfg, num_sms, stream);
-            else
-                rc = bk == 64 ? launch_variant<128, 64, 3, true>(a, b, p, cfg, num_sms, stream)
-                              : launch_variant<128, 32, 3, true>(a, b, p, cfg, num_sms, stream);
-        } else {
-            if (bn == 256)
-                rc = bk == 64 ? launch_variant<256, 64, 3, false>(a, b, p, cfg, num_sms, stream)
-                              : launch_variant<256, 32, 3, false>(a, b, p, cfg, num_sms, stream);
-            else
-                rc = bk == 64 ? launch_variant<128, 64, 3, false>(a, b, p, cfg, num_sms, stream)
-                              : launch_variant<128, 32, 3, false>(a, b, p, cfg, num_sms, stream);
-        }
-    } else {
-        if (bn == 256)
-            rc = bk == 64 ? launch_variant<256, 64, 1, false>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<256, 32, 1, false>(a, b, p, cfg, num_sms, stream);
-        else
-            rc = bk == 64 ? launch_variant<128, 64, 1, false>(a, b, p, cfg, num_sms, stream)
-                          : launch_variant<128, 32, 1, false>(a, b, p, cfg, num_sms, stream);
-    }
+    const int rc = dispatch<false>(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream);
     if (rc != 0) return rc;
     int n = 1;
     if (split > 1) {
@@ -526,6 +600,24 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     }
     if (launches) *launches += n;
     return 0;
+}
+
+int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev_problems,
+                      const CUtensorMap* dev_maps, int count, int total_tiles, int* err_word,
+                      int num_sms, cudaStream_t stream) {
+    if (count <= 0 || total_tiles <= 0) return 0;
+    const int bn = cfg.bn == 128 ? 128 : 256;
+    const int bk = cfg.bk == 64 ? 64 : 32;
+    TcParams p{};
+    p.num_tiles = total_tiles;
+    p.split_k = 1;
+    p.problems = dev_problems;
+    p.maps = dev_maps;
+    p.count = count;
+    fill_common(p, cfg, bk, nterms, err_word);
+    CUtensorMap unused{};  // grouped kernels read their maps from dev_maps
+    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    return dispatch<true>(nterms, promote, bn, bk, unused, unused, p, cfg, num_sms, stream);
 }
 
 }  // namespace gb300

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import MODES, OP_N, OP_T, check, gemm_config_t, gemm_problem_t
 
 __all__ = ["Gemm", "handle", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
-           "gemm_backward", "gemm_grouped", "GemmFn", "sync"]
+           "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "sync"]
 
 
 def _mode(mode):
@@ -223,13 +223,9 @@ def gemm_backward(dC, A, B, transA=False, transB=False, need_dA=True, need_dB=Tr
     return dA, dB
 
 
-def gemm_grouped(problems, mode="bf16x3", h=None):
-    """problems: list of dicts with A, B, C (CUDA tensors) and optional
-    alpha, beta, transA, transB.  C tensors are updated in place."""
-    h = h or handle()
+def _problem_array(problems):
     arr = (gemm_problem_t * len(problems))()
-    ws = 0
-    m = _mode(mode)
+    keep = []
     for i, p in enumerate(problems):
         A, B, C = p["A"], p["B"], p["C"]
         tA, tB = int(p.get("transA", False)), int(p.get("transB", False))
@@ -237,10 +233,59 @@ def gemm_grouped(problems, mode="bf16x3", h=None):
         arr[i] = gemm_problem_t(M, N, K, _ld(A), _ld(B), _ld(C), A.data_ptr(), B.data_ptr(),
                                 C.data_ptr(), float(p.get("alpha", 1.0)),
                                 float(p.get("beta", 0.0)), tA, tB)
-    ws = h.lib.gemm_grouped_workspace_size(h.h, m, arr, len(problems)) \
-        if hasattr(h.lib, "gemm_grouped_workspace_size") else 0
-    h.ensure_workspace(ws)
-    st = h.lib.gemm_grouped(h.h, m, arr, len(problems), _stream(h.device))
+        keep.append((A, B, C))
+    return arr, keep
+
+
+class GroupedPlan:
+    """gemm_grouped_plan_*: many independent GEMMs (dicts with A, B, C CUDA
+    tensors and optional alpha, beta, transA, transB) run as one split launch
+    plus one persistent tensor-core launch.  autotune: time the candidate
+    configurations at creation; graph: capture the launches in a CUDA graph
+    on the first run and replay it."""
+
+    def __init__(self, problems, mode="bf16x3", autotune=False, graph=False, h=None,
+                 stream=None):
+        self.h = h or handle(problems[0]["A"].device if problems else None)
+        self.lib = self.h.lib
+        self._arr, self._keep = _problem_array(problems)
+        flags = (_lib.GROUPED_AUTOTUNE if autotune else 0) | (_lib.GROUPED_GRAPH if graph else 0)
+        s = _stream(self.h.device) if stream is None else ctypes.c_void_p(stream)
+        plan = ctypes.c_void_p()
+        st = self.lib.gemm_grouped_plan_create(self.h.h, _mode(mode), self._arr, len(problems),
+                                               flags, s, ctypes.byref(plan))
+        check(st, "gemm_grouped_plan_create", self.h.h)
+        self.plan = plan
+
+    def run(self, stream=None):
+        s = _stream(self.h.device) if stream is None else ctypes.c_void_p(stream)
+        check(self.lib.gemm_grouped_plan_run(self.plan, s), "gemm_grouped_plan_run", self.h.h)
+
+    def config(self):
+        cfg = gemm_config_t()
+        ms = ctypes.c_double()
+        check(self.lib.gemm_grouped_plan_config(self.plan, ctypes.byref(cfg), ctypes.byref(ms)),
+              "gemm_grouped_plan_config")
+        return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
+                "raster_group": cfg.raster_group, "tuned_ms": ms.value}
+
+    def close(self):
+        if self.plan:
+            self.lib.gemm_grouped_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_grouped(problems, mode="bf16x3", h=None):
+    """One-shot grouped GEMM (builds, runs and frees a plan; synchronises)."""
+    h = h or handle()
+    arr, keep = _problem_array(problems)
+    st = h.lib.gemm_grouped(h.h, _mode(mode), arr, len(problems), _stream(h.device))
     check(st, "gemm_grouped", h.h)
 
 

@@ -1,0 +1,206 @@
+"""Grouped GEMM (gemm_grouped and the plan API) against the FP64 oracle:
+uneven problems in one persistent launch, autotuned vs fixed configuration,
+CUDA-graph replay vs eager (GB300 only)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_18236_gb300 import inputs
+from tests.gpu_util import tol_exact, tol_terms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2305_18236_gb300 import build
+
+    build.build()
+
+
+def make_problems(count, seed, lo=64, hi=512, dist="uniform", ragged=True, mixed=True):
+    """Uneven problems: M, N, K multiples of 32 in [lo, hi] (plus a ragged
+    offset on some), all transpose combinations, per-problem alpha/beta."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        M, N, K = (int(x) * 32 for x in rng.integers(lo // 32, hi // 32 + 1, size=3))
+        if ragged and i % 3 == 1:
+            M, N, K = M - 5, N - 11, K - 3
+        tA = bool(i % 2) if mixed else False
+        tB = bool((i // 2) % 2) if mixed else False
+        alpha, beta = (1.5, 0.5) if mixed and i % 4 == 3 else (1.0, 0.0)
+        A = inputs.make(dist, (K, M) if tA else (M, K), seed * 1000 + 3 * i, k=K)
+        B = inputs.make(dist, (N, K) if tB else (K, N), seed * 1000 + 3 * i + 1, k=K)
+        C0 = inputs.uniform((M, N), seed * 1000 + 3 * i + 2)
+        out.append(dict(A=A, B=B, C0=C0, transA=tA, transB=tB, alpha=alpha, beta=beta, M=M, N=N,
+                        K=K))
+    return out
+
+
+def to_device(problems):
+    import torch
+
+    dev = []
+    for p in problems:
+        dev.append(dict(A=torch.from_numpy(p["A"]).cuda(), B=torch.from_numpy(p["B"]).cuda(),
+                        C=torch.from_numpy(p["C0"].copy()).cuda(), transA=p["transA"],
+                        transB=p["transB"], alpha=p["alpha"], beta=p["beta"]))
+    return dev
+
+
+def check_against_oracle(problems, dev, mode, rows_per=None):
+    import torch
+
+    torch.cuda.synchronize()
+    for p, d in zip(problems, dev):
+        rows = None if rows_per is None else np.linspace(0, p["M"] - 1, rows_per).astype(np.int64)
+        C64, D, _ = oracle.gemm(p["A"], p["B"], p["alpha"], p["beta"], p["C0"],
+                                transA=p["transA"], transB=p["transB"], rows=rows)
+        out = d["C"].cpu().numpy()
+        out = out if rows is None else out[rows]
+        assert oracle.normwise_error(out, C64, D) <= tol_exact(mode, p["K"])
+        terms = 1 if mode == "bf16" else 7
+        T64 = oracle.gemm_split_terms(p["A"], p["B"], terms, p["alpha"], p["beta"], p["C0"],
+                                      transA=p["transA"], transB=p["transB"], rows=rows)
+        assert oracle.normwise_error(out, T64, D) <= tol_terms(mode, p["K"])
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_grouped_uneven_problems(mode):
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = make_problems(24, 11)
+    dev = to_device(probs)
+    g.gemm_grouped(dev, mode=mode)
+    check_against_oracle(probs, dev, mode)
+
+
+def test_grouped_integer_bit_exact_autotuned_and_fixed():
+    """Integer data: every configuration the autotuner may pick gives the
+    oracle's result bit for bit; the tuned and the fixed plan agree."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    rng = np.random.default_rng(5)
+    probs = []
+    for i in range(16):
+        M, N, K = (int(x) * 32 for x in rng.integers(2, 17, size=3))
+        probs.append(dict(A=inputs.integers((M, K), 40 + i), B=inputs.integers((K, N), 80 + i),
+                          C0=inputs.integers((M, N), 120 + i), transA=False, transB=False,
+                          alpha=1.5, beta=0.5, M=M, N=N, K=K))
+    results = []
+    for autotune in (False, True):
+        dev = to_device(probs)
+        plan = g.GroupedPlan(dev, mode="bf16x3", autotune=autotune)
+        plan.run()
+        torch.cuda.synchronize()
+        results.append([d["C"].cpu().numpy() for d in dev])
+        cfg = plan.config()
+        assert cfg["bn"] in (128, 256) and cfg["bk"] in (32, 64)
+        plan.close()
+    for p, a, b in zip(probs, results[0], results[1]):
+        ref, _, _ = oracle.gemm(p["A"], p["B"], 1.5, 0.5, p["C0"])
+        assert np.array_equal(a.astype(np.float64), ref)
+        assert np.array_equal(b.astype(np.float64), ref)
+
+
+def test_grouped_graph_replay_equals_eager():
+    """A graph-captured plan replayed twice on beta = 0 problems equals an
+    eager run, bit for bit; with beta != 0 each replay applies the update
+    again (C <- alpha AB + beta C), as an eager run would."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = make_problems(12, 21, mixed=False)
+    dev_e = to_device(probs)
+    dev_g = to_device(probs)
+    eager = g.GroupedPlan(dev_e, mode="bf16x3")
+    graph = g.GroupedPlan(dev_g, mode="bf16x3", graph=True)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        eager.run()
+        graph.run()  # captures, then replays
+        graph.run()  # replays again: beta = 0, same result
+    stream.synchronize()
+    for a, b in zip(dev_e, dev_g):
+        assert torch.equal(a["C"], b["C"])
+    check_against_oracle(probs, dev_g, "bf16x3")
+    eager.close()
+    graph.close()
+
+
+def test_grouped_degenerate_problems():
+    """Problems with M = 0, K = 0 or alpha = 0 mixed with ordinary ones."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = make_problems(6, 31, mixed=False)
+    dev = to_device(probs)
+    z = dict(A=torch.zeros((0, 16), device="cuda"), B=torch.zeros((16, 8), device="cuda"),
+             C=torch.zeros((0, 8), device="cuda"))
+    C_k0 = torch.from_numpy(inputs.uniform((40, 24), 7)).cuda()
+    k0 = dict(A=torch.zeros((40, 0), device="cuda"), B=torch.zeros((0, 24), device="cuda"),
+              C=C_k0, beta=0.25)
+    C_a0 = torch.from_numpy(inputs.uniform((33, 17), 8)).cuda()
+    a0 = dict(A=torch.full((33, 9), float("nan"), device="cuda"),
+              B=torch.full((9, 17), float("nan"), device="cuda"), C=C_a0, alpha=0.0, beta=2.0)
+    ref_k0 = 0.25 * C_k0.clone()
+    ref_a0 = 2.0 * C_a0.clone()
+    g.gemm_grouped([z] + dev[:3] + [k0, a0] + dev[3:], mode="bf16x3")
+    torch.cuda.synchronize()
+    assert torch.equal(C_k0, ref_k0)
+    assert torch.equal(C_a0, ref_a0)
+    check_against_oracle(probs, dev, "bf16x3")
+
+
+def test_grouped_bad_problem_position():
+    import ctypes
+
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = make_problems(4, 41, mixed=False)
+    dev = to_device(probs)
+    arr, keep = g._problem_array(dev)
+    arr[2].ldc = 1  # smaller than N
+    h = g.handle()
+    plan = ctypes.c_void_p()
+    st = h.lib.gemm_grouped_plan_create(h.h, 2, arr, 4, 0, None, ctypes.byref(plan))
+    assert st == _lib.GEMM_ERR_ARG
+    assert h.last_error_arg() == 102
+
+
+def test_grouped_config4_shapes_sampled():
+    """512 problems with M, N, K uniform multiples of 32 in [64, 2048]
+    (FP32, 3xBF16, alpha = 1, beta = 0), autotuned and graph-captured;
+    eight problems checked against the oracle on sampled rows."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    rng = np.random.default_rng(0x5EED)
+    shapes = [tuple(int(x) * 32 for x in rng.integers(2, 65, size=3)) for _ in range(512)]
+    dev = []
+    for i, (M, N, K) in enumerate(shapes):
+        gen = torch.Generator(device="cuda").manual_seed(1000 + i)
+        A = torch.rand((M, K), device="cuda", generator=gen) * 2 - 1
+        B = torch.rand((K, N), device="cuda", generator=gen) * 2 - 1
+        dev.append(dict(A=A, B=B, C=torch.empty((M, N), device="cuda")))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = g.GroupedPlan(dev, mode="bf16x3", autotune=True, graph=True)
+        plan.run()
+    stream.synchronize()
+    for i in np.linspace(0, 511, 8).astype(int):
+        M, N, K = shapes[i]
+        A = dev[i]["A"].cpu().numpy()
+        B = dev[i]["B"].cpu().numpy()
+        rows = np.linspace(0, M - 1, 6).astype(np.int64)
+        C64, D, _ = oracle.gemm(A, B, rows=rows)
+        out = dev[i]["C"].cpu().numpy()[rows]
+        assert oracle.normwise_error(out, C64, D) <= tol_exact("bf16x3", K)
+    plan.close()
