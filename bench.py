@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-compare", action="store_true", help="skip the FP32 SIMT comparison")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--workload", default="square", choices=["square", "rect", "grouped", "chain"],
+                   help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
+                        "grouped: 512 uneven problems; chain: Y = X W forward + backward")
     return p.parse_args()
 
 
@@ -152,6 +155,14 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def square_config(n, mode, world):
+    """The workload description shared by both arms of the headline line."""
+    return {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
+                        % (n, n, n),
+            "mode": mode, "M": n, "N": n, "K": n, "parallelism": "replicas x%d" % world,
+            "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush"}
+
+
 def make_inputs(n):
     from paper_2305_18236_gb300 import inputs
 
@@ -236,8 +247,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5 U[-1,1]" % (n, n, n),
-                   "M": n, "N": n, "K": n, "sample_rows_per_step": rows_per_step},
+        "config": square_config(n, args.mode, world),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -374,11 +384,8 @@ def run_ours(args):
         "dtype": {"bf16x3": "bf16x3 (bf16 hi/lo products, f32 accumulate)",
                   "bf16": "bf16 (f32 accumulate)", "f32_simt": "f32"}[mode],
         "data": "synthetic",
-        "config": {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
-                               % (n, n, n),
-                   "mode": mode, "M": M, "N": N, "K": K, "parallelism": "replicas x%d" % world,
-                   "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush",
-                   "launches_per_step": launches_per_step},
+        "config": square_config(n, mode, world),
+        "launches_per_step": launches_per_step,
         "roofline": roof,
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
@@ -397,10 +404,150 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------- other workloads
+def _events_ms(fn, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_rect(args):
+    """BF16-input rectangular/skinny GEMMs (FP32 accumulate and output),
+    entries N(0, 1/sqrt(K)), alpha = 1, beta = 0, through gemm_bf16."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+
+    torch.cuda.set_device(0)
+    peaks, src = load_peaks()
+    stream = torch.cuda.current_stream()
+    out = []
+    for (M, N, K) in [(16384, 4096, 1024), (4096, 16384, 4096), (128, 8192, 8192),
+                      (8192, 8192, 64)]:
+        gen = torch.Generator(device="cuda").manual_seed(SEED)
+        A = (torch.randn((M, K), device="cuda", generator=gen) / np.sqrt(K)).to(torch.bfloat16)
+        B = (torch.randn((N, K), device="cuda", generator=gen) / np.sqrt(K)).to(torch.bfloat16)
+        C = torch.empty((M, N), device="cuda")
+        # B stored N x K (transB): both operands K-contiguous, read in place by TMA
+        ms = _events_ms(lambda: g.matmul_bf16(A, B, C=C, transB=True), args.steps, args.warmup,
+                        stream)
+        flops = 2.0 * M * N * K
+        nbytes = 2.0 * (M * K + N * K) + 4.0 * M * N
+        out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
+                    "gbs": nbytes / ms / 1e6,
+                    "frac_tensor": flops / ms / 1e9 / peaks["bf16_tflops"],
+                    "frac_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"],
+                    "launches": g.handle().last_launch_count()})
+    tot_flops = sum(2.0 * r["M"] * r["N"] * r["K"] for r in out)
+    tot_ms = sum(r["ms"] for r in out)
+    print(json.dumps({"metric": "rectangular BF16-input GEMM TFLOP/s (sum over 4 shapes)",
+                      "value": tot_flops / tot_ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": "bf16 in, f32 accumulate/out", "data": "synthetic",
+                      "config": {"workload": "bf16 NT shapes, N(0,1/sqrt(K))"},
+                      "shapes": out, "peaks_source": src}), flush=True)
+
+
+def run_grouped(args):
+    """512 problems, M, N, K uniform multiples of 32 in [64, 2048], FP32,
+    3xBF16, alpha = 1, beta = 0: autotuned + graph-captured plan vs the fixed
+    default configuration (eager)."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(SEED)
+    shapes = [tuple(int(x) * 32 for x in rng.integers(2, 65, size=3)) for _ in range(512)]
+    probs = []
+    for i, (M, N, K) in enumerate(shapes):
+        gen = torch.Generator(device="cuda").manual_seed(SEED + i)
+        probs.append(dict(A=torch.rand((M, K), device="cuda", generator=gen) * 2 - 1,
+                          B=torch.rand((K, N), device="cuda", generator=gen) * 2 - 1,
+                          C=torch.empty((M, N), device="cuda")))
+    flops = sum(2.0 * M * N * K for (M, N, K) in shapes)
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, kw in [("fixed_eager", dict()), ("fixed_graph", dict(graph=True)),
+                         ("tuned_graph", dict(autotune=True, graph=True))]:
+            t0 = time.perf_counter()
+            plan = g.GroupedPlan(probs, mode=args.mode, **kw)
+            create_s = time.perf_counter() - t0
+            ms = _events_ms(plan.run, args.steps, args.warmup, stream)
+            res[name] = {"ms": ms, "tflops": flops / ms / 1e9, "config": plan.config(),
+                         "plan_create_s": create_s}
+            plan.close()
+    best = res["tuned_graph"]
+    print(json.dumps({"metric": "grouped GEMM TFLOP/s, 512 problems (2MNK summed)",
+                      "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
+                      "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
+                      "config": {"workload": "512 problems, M,N,K ~ 32*U{2..64}, FP32 U[-1,1]",
+                                 "flops_per_step": flops},
+                      "variants": res}), flush=True)
+
+
+def run_chain(args):
+    """Y = X W, loss = sum(Y * G), forward + backward through GemmFn:
+    X 8192x4096, W 4096x4096, G 8192x4096, FP32 N(0, 1/sqrt(4096))."""
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+
+    torch.cuda.set_device(0)
+    gen = torch.Generator(device="cuda").manual_seed(SEED)
+    X = (torch.randn((8192, 4096), device="cuda", generator=gen) / 64.0).requires_grad_(True)
+    W = (torch.randn((4096, 4096), device="cuda", generator=gen) / 64.0).requires_grad_(True)
+    G = torch.randn((8192, 4096), device="cuda", generator=gen) / 64.0
+
+    def step():
+        X.grad = None
+        W.grad = None
+        Y = g.GemmFn.apply(X, W, args.mode)
+        Y.backward(G)
+
+    ms = _events_ms(step, args.steps, args.warmup, torch.cuda.current_stream())
+    flops = 3 * 2.0 * 8192 * 4096 * 4096
+    print(json.dumps({"metric": "differentiable GEMM chain TFLOP/s (forward + backward)",
+                      "value": flops / ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
+                      "config": {"workload": "X 8192x4096, W 4096x4096, dY = G; fwd + dX + dW"}}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "rect":
+        run_rect(args)
+    elif args.workload == "grouped":
+        run_grouped(args)
+    elif args.workload == "chain":
+        run_chain(args)
     else:
         run_ours(args)
 

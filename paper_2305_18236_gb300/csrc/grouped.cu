@@ -41,6 +41,8 @@ struct gemm_grouped_plan_s {
     gb300::SplitJob* d_jobs = nullptr;
     gb300::GroupedProblem* d_probs = nullptr;
     CUtensorMap* d_maps = nullptr;
+    int* d_tile_prob = nullptr;
+    int* d_tile_job = nullptr;
     int njobs = 0, split_tiles = 0, nprobs = 0, total_tiles = 0;
     // problems handled by a plain scale (K == 0 or alpha == 0)
     struct Scale {
@@ -75,8 +77,9 @@ struct HostProb {
 // Problem table and tensor maps for a tile shape; returns total tiles.
 int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
                  std::vector<GroupedProblem>& probs, std::vector<CUtensorMap>& maps,
-                 bool* ok) {
+                 std::vector<int>& tile_prob, bool* ok) {
     probs.clear();
+    tile_prob.clear();
     maps.assign(2 * ps.size(), CUtensorMap{});
     int tiles = 0;
     *ok = true;
@@ -95,6 +98,7 @@ int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
         g.alpha = q.alpha;
         g.beta = q.beta;
         tiles += g.num_m * g.num_n;
+        tile_prob.insert(tile_prob.end(), size_t(g.num_m) * g.num_n, int(i));
         probs.push_back(g);
         if (!gb300::encode_operand(&maps[2 * i], q.a, bk, 128) ||
             !gb300::encode_operand(&maps[2 * i + 1], q.b, bk, bn))
@@ -231,6 +235,8 @@ void free_plan(gemm_grouped_plan_s* p) {
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_probs) cudaFree(p->d_probs);
     if (p->d_maps) cudaFree(p->d_maps);
+    if (p->d_tile_prob) cudaFree(p->d_tile_prob);
+    if (p->d_tile_job) cudaFree(p->d_tile_job);
     delete p;
 }
 
@@ -240,19 +246,22 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
                       int* err_word, int num_sms, cudaStream_t s) {
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
+    std::vector<int> tile_prob;
     bool ok = true;
-    const int tiles = build_tables(sub, cfg.bn, cfg.bk, nterms, probs, maps, &ok);
+    const int tiles = build_tables(sub, cfg.bn, cfg.bk, nterms, probs, maps, tile_prob, &ok);
     if (!ok) return -1.0;
     GroupedProblem* dp = nullptr;
     CUtensorMap* dm = nullptr;
+    int* dt = nullptr;
     double best = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (upload(&dp, probs, s) == GEMM_OK && upload(&dm, maps, s) == GEMM_OK &&
+        upload(&dt, tile_prob, s) == GEMM_OK &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, s);
-            const int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, int(sub.size()), tiles,
-                                                    err_word, num_sms, s);
+            const int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, dt, int(sub.size()),
+                                                    tiles, err_word, num_sms, s);
             cudaEventRecord(e1, s);
             if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
                 best = -1.0;
@@ -268,6 +277,7 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
     if (e1) cudaEventDestroy(e1);
     if (dp) cudaFree(dp);
     if (dm) cudaFree(dm);
+    if (dt) cudaFree(dt);
     return best;
 }
 
@@ -275,11 +285,12 @@ gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
     for (const auto& sc : p->scales)
         if (gb300::launch_scale_c(sc.M, sc.N, sc.beta, sc.C, sc.ldc, s) != cudaSuccess)
             return GEMM_ERR_CUDA;
-    if (gb300::launch_split_grouped(p->d_jobs, p->njobs, p->split_tiles, p->num_sms, s) !=
-        cudaSuccess)
+    if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
+                                    p->num_sms, s) != cudaSuccess)
         return GEMM_ERR_CUDA;
-    const int rc = gb300::launch_tc_grouped(p->nterms, p->cfg, p->d_probs, p->d_maps, p->nprobs,
-                                            p->total_tiles, p->err_word, p->num_sms, s);
+    const int rc = gb300::launch_tc_grouped(p->nterms, p->cfg, p->d_probs, p->d_maps,
+                                            p->d_tile_prob, p->nprobs, p->total_tiles,
+                                            p->err_word, p->num_sms, s);
     return rc == 0 ? GEMM_OK : static_cast<gemm_status_t>(rc);
 }
 
@@ -343,6 +354,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     // workspace layout: per problem, A planes [planes][M][Kp] then B planes [planes][N][Kp]
     std::vector<HostProb> ps;
     std::vector<SplitJob> jobs;
+    std::vector<int> tile_job;
     std::vector<size_t> a_off, b_off;
     size_t ws = 0;
     for (int i = 0; i < count; ++i) {
@@ -385,6 +397,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         ja.tiles_r = int((q.M + 63) / 64);
         ja.tile_start = tiles;
         tiles += ja.tiles_r * int((q.K + 63) / 64);
+        tile_job.insert(tile_job.end(), size_t(ja.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
         jobs.push_back(ja);
         SplitJob jb{};
         jb.src = q.B;
@@ -399,6 +412,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         jb.tiles_r = int((q.N + 63) / 64);
         jb.tile_start = tiles;
         tiles += jb.tiles_r * int((q.K + 63) / 64);
+        tile_job.insert(tile_job.end(), size_t(jb.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
         jobs.push_back(jb);
         HostProb hq;
         hq.a = TcOperand{ah, q.M, q.K, kp, q.M * kp, planes};
@@ -416,6 +430,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     p->split_tiles = tiles;
     p->nprobs = int(ps.size());
     gemm_status_t st = upload(&p->d_jobs, jobs, s);
+    if (st == GEMM_OK) st = upload(&p->d_tile_job, tile_job, s);
     if (st != GEMM_OK) {
         free_plan(p);
         return st;
@@ -431,8 +446,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->cfg.raster_group = hit.raster_group;
         } else {
             // operands must be split before the candidates can be timed
-            if (gb300::launch_split_grouped(p->d_jobs, p->njobs, p->split_tiles, p->num_sms, s) !=
-                cudaSuccess) {
+            if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
+                                            p->num_sms, s) != cudaSuccess) {
                 free_plan(p);
                 return GEMM_ERR_CUDA;
             }
@@ -486,13 +501,16 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
 
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
+    std::vector<int> tile_prob;
     bool ok = true;
-    p->total_tiles = build_tables(ps, p->cfg.bn, p->cfg.bk, nterms, probs, maps, &ok);
+    p->total_tiles = build_tables(ps, p->cfg.bn, p->cfg.bk, nterms, probs, maps, tile_prob, &ok);
     if (!ok) {
         free_plan(p);
         return GEMM_ERR_CUDA;
     }
-    if ((st = upload(&p->d_probs, probs, s)) != GEMM_OK || (st = upload(&p->d_maps, maps, s)) != GEMM_OK) {
+    if ((st = upload(&p->d_probs, probs, s)) != GEMM_OK ||
+        (st = upload(&p->d_maps, maps, s)) != GEMM_OK ||
+        (st = upload(&p->d_tile_prob, tile_prob, s)) != GEMM_OK) {
         free_plan(p);
         return st;
     }

@@ -52,10 +52,11 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
 
 // Grouped launch: `count` problems described by dev_problems (device) with
 // two tensor maps each in dev_maps (device, encoded with cfg.bk and a box of
-// 128 rows for A and cfg.bn rows for B); total_tiles = sum of num_m * num_n.
+// 128 rows for A and cfg.bn rows for B); total_tiles = sum of num_m * num_n;
+// dev_tile_prob[t] = index of the problem that owns tile t.
 int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev_problems,
-                      const CUtensorMap* dev_maps, int count, int total_tiles, int* err_word,
-                      int num_sms, cudaStream_t stream);
+                      const CUtensorMap* dev_maps, const int* dev_tile_prob, int count,
+                      int total_tiles, int* err_word, int num_sms, cudaStream_t stream);
 
 // Dynamic shared memory the tensor-core kernel asks for with this config
 // (0 if the configuration does not exist).
@@ -95,9 +96,10 @@ struct SplitJob {
     int tiles_r;  // (rows + 63) / 64
 };
 
-// Split every job of the table in one launch (total_tiles 64 x 64 tiles).
-cudaError_t launch_split_grouped(const SplitJob* dev_jobs, int njobs, int total_tiles,
-                                 int num_sms, cudaStream_t stream);
+// Split every job of the table in one launch (total_tiles 64 x 64 tiles;
+// dev_tile_job[t] = index of the job that owns tile t).
+cudaError_t launch_split_grouped(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
+                                 int total_tiles, int num_sms, cudaStream_t stream);
 
 // Y = op(X) for BF16 X (a pure re-layout), rows x cols, row stride ldo.
 cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,

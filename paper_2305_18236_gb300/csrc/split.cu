@@ -211,26 +211,24 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N
 }
 
 // Grouped split: the concatenated 64 x 64 output tiles of all jobs; each
-// block finds its job by binary search over the prefix sums.  Transposed
+// tile finds its job in the host-built tile -> job map.  Transposed
 // jobs go through a shared-memory tile; the others convert straight along
 // the rows (each thread 16 consecutive elements of one row).
-__global__ void __launch_bounds__(256) split_grouped_kernel(const SplitJob* __restrict__ jobs,
-                                                            int njobs, int total_tiles) {
+__global__ void __launch_bounds__(256, 8) split_grouped_kernel(const SplitJob* __restrict__ jobs,
+                                                            const int* __restrict__ tile_job,
+                                                            int total_tiles) {
     __shared__ float tile[64][65];
     const int tid = threadIdx.x;
+    // grid-stride over tiles, so concurrently running blocks work on
+    // neighbouring tiles of the same source rows (DRAM page locality)
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-        int lo_j = 0, hi_j = njobs - 1;
-        while (lo_j < hi_j) {
-            const int mid = (lo_j + hi_j + 1) >> 1;
-            if (__ldg(&jobs[mid].tile_start) <= t)
-                lo_j = mid;
-            else
-                hi_j = mid - 1;
-        }
-        const SplitJob& j = jobs[lo_j];
+        const SplitJob& j = jobs[__ldg(&tile_job[t])];
+        // neighbouring tiles are neighbours along the source's rows: along
+        // Y's rows (r0) for a transposed job, along Y's columns (c0) otherwise
         const int local = t - j.tile_start;
-        const int64_t r0 = int64_t(local % j.tiles_r) * 64;
-        const int64_t c0 = int64_t(local / j.tiles_r) * 64;
+        const int tiles_c = (j.cols + 63) / 64;
+        const int64_t r0 = int64_t(j.trans ? local % j.tiles_r : local / tiles_c) * 64;
+        const int64_t c0 = int64_t(j.trans ? local / j.tiles_r : local % tiles_c) * 64;
         if (j.trans) {
             // X is cols x rows: read X rows c0.., columns r0.. coalesced
 #pragma unroll
@@ -269,41 +267,37 @@ __global__ void __launch_bounds__(256) split_grouped_kernel(const SplitJob* __re
             }
             __syncthreads();
         } else {
-            const int64_t yr = r0 + (tid >> 2);
-            const int64_t yc = c0 + (tid & 3) * 16;
-            if (yr < j.rows && yc < j.cols) {
-                const float* src = j.src + yr * j.ldx + yc;
-                float v[16];
-                if (j.x_vec && yc + 16 <= j.cols) {
+            // 64 rows x 16 float4 per tile; float4 f = q*256 + tid, so a warp
+            // reads two whole 256-byte row segments per instruction
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 a = __ldcs(reinterpret_cast<const float4*>(src) + q);
-                        v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+            for (int q = 0; q < 4; ++q) {
+                const int f = q * 256 + tid;
+                const int64_t yr = r0 + (f >> 4);
+                const int64_t yc = c0 + (f & 15) * 4;
+                if (yr < j.rows && yc < j.cols) {
+                    const float* src = j.src + yr * j.ldx + yc;
+                    float v[4];
+                    if (j.x_vec && yc + 4 <= j.cols) {
+                        const float4 a = __ldcs(reinterpret_cast<const float4*>(src));
+                        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = yc + e < j.cols ? src[e] : 0.0f;
                     }
-                } else {
+                    uint16_t h[4], l[4];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = yc + q < j.cols ? src[q] : 0.0f;
-                }
-                uint16_t h[16], l[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) split1(v[q], h[q], l[q]);
-                uint16_t* dh = j.hi + yr * j.ldo + yc;
-                uint16_t* dl = j.lo ? j.lo + yr * j.ldo + yc : nullptr;
-                if (yc + 16 <= j.cols) {
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        reinterpret_cast<uint4*>(dh)[q] =
-                            make_uint4(pack2(h[8 * q], h[8 * q + 1]), pack2(h[8 * q + 2], h[8 * q + 3]),
-                                       pack2(h[8 * q + 4], h[8 * q + 5]), pack2(h[8 * q + 6], h[8 * q + 7]));
+                    for (int e = 0; e < 4; ++e) split1(v[e], h[e], l[e]);
+                    uint16_t* dh = j.hi + yr * j.ldo + yc;
+                    uint16_t* dl = j.lo ? j.lo + yr * j.ldo + yc : nullptr;
+                    if (yc + 4 <= j.cols) {  // ldo % 8 == 0 and yc % 4 == 0: 8-byte aligned
+                        *reinterpret_cast<uint2*>(dh) = make_uint2(pack2(h[0], h[1]), pack2(h[2], h[3]));
                         if (dl)
-                            reinterpret_cast<uint4*>(dl)[q] = make_uint4(
-                                pack2(l[8 * q], l[8 * q + 1]), pack2(l[8 * q + 2], l[8 * q + 3]),
-                                pack2(l[8 * q + 4], l[8 * q + 5]), pack2(l[8 * q + 6], l[8 * q + 7]));
-                    }
-                } else {
-                    for (int q = 0; q < 16 && yc + q < j.cols; ++q) {
-                        dh[q] = h[q];
-                        if (dl) dl[q] = l[q];
+                            *reinterpret_cast<uint2*>(dl) = make_uint2(pack2(l[0], l[1]), pack2(l[2], l[3]));
+                    } else {
+                        for (int e = 0; e < 4 && yc + e < j.cols; ++e) {
+                            dh[e] = h[e];
+                            if (dl) dl[e] = l[e];
+                        }
                     }
                 }
             }
@@ -313,11 +307,11 @@ __global__ void __launch_bounds__(256) split_grouped_kernel(const SplitJob* __re
 
 }  // namespace
 
-cudaError_t launch_split_grouped(const SplitJob* dev_jobs, int njobs, int total_tiles,
-                                 int num_sms, cudaStream_t stream) {
+cudaError_t launch_split_grouped(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
+                                 int total_tiles, int num_sms, cudaStream_t stream) {
     if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
-    const int grid = std::max(1, std::min(total_tiles, num_sms * 8));
-    split_grouped_kernel<<<grid, 256, 0, stream>>>(dev_jobs, njobs, total_tiles);
+    const int grid = std::max(1, std::min(total_tiles, num_sms * 16));
+    split_grouped_kernel<<<grid, 256, 0, stream>>>(dev_jobs, dev_tile_job, total_tiles);
     return cudaGetLastError();
 }
 

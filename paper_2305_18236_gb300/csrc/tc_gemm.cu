@@ -63,6 +63,7 @@ struct TcParams {
     // tensor maps per problem (A then B), all in device memory
     const GroupedProblem* problems;
     const CUtensorMap* maps;
+    const int* tile_prob;  // problem index of every tile
     int count;
 };
 
@@ -128,15 +129,7 @@ __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUt
         ti.ma = tmA;
         ti.mb = tmB;
     } else {
-        // last problem whose first tile is <= t
-        int lo = 0, hi = p.count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&p.problems[mid].tile_start) <= t)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
+        const int lo = __ldg(&p.tile_prob[t]);
         const GroupedProblem* q = p.problems + lo;
         ti.ks = 0;
         raster(t - __ldg(&q->tile_start), __ldg(&q->num_m), __ldg(&q->num_n), p.raster_group,
@@ -603,8 +596,8 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
 }
 
 int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev_problems,
-                      const CUtensorMap* dev_maps, int count, int total_tiles, int* err_word,
-                      int num_sms, cudaStream_t stream) {
+                      const CUtensorMap* dev_maps, const int* dev_tile_prob, int count,
+                      int total_tiles, int* err_word, int num_sms, cudaStream_t stream) {
     if (count <= 0 || total_tiles <= 0) return 0;
     const int bn = cfg.bn == 128 ? 128 : 256;
     const int bk = cfg.bk == 64 ? 64 : 32;
@@ -613,6 +606,7 @@ int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev
     p.split_k = 1;
     p.problems = dev_problems;
     p.maps = dev_maps;
+    p.tile_prob = dev_tile_prob;
     p.count = count;
     fill_common(p, cfg, bk, nterms, err_word);
     CUtensorMap unused{};  // grouped kernels read their maps from dev_maps
