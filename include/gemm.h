@@ -83,6 +83,9 @@ typedef struct gemm_context *gemm_handle_t;
  *    before the partial sum is added into FP32 registers with round-to-
  *    nearest (0 = default 512, -1 = never; the tensor core's own FP32
  *    accumulation rounds toward zero, so long chains lose accuracy).
+ *  cta_group: 1 = one CTA per 128-row tile; 2 = CTA pairs (a cluster of two
+ *    SMs shares a 256-row tile, each staging half of B; bn must be 256);
+ *    0 = library choice.
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
  *    the device error word and exits cleanly (0 = default, about seconds). */
 typedef struct {
@@ -93,7 +96,7 @@ typedef struct {
     int32_t raster_group;
     int32_t max_ctas;
     int32_t promote_k;
-    int32_t reserved; /* must be 0 */
+    int32_t cta_group;
     int64_t wait_poll_limit;
 } gemm_config_t;
 

@@ -32,7 +32,7 @@ _i32, _i64, _f32, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, cty
 class gemm_config_t(ctypes.Structure):
     _fields_ = [("bn", _i32), ("bk", _i32), ("stages", _i32), ("split_k", _i32),
                 ("raster_group", _i32), ("max_ctas", _i32), ("promote_k", _i32),
-                ("reserved", _i32), ("wait_poll_limit", _i64)]
+                ("cta_group", _i32), ("wait_poll_limit", _i64)]
 
 
 class gemm_problem_t(ctypes.Structure):

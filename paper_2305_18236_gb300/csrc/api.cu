@@ -63,6 +63,7 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
     c.max_ctas = h->cfg.max_ctas;
     c.poll_limit = h->cfg.wait_poll_limit;
     c.promote_k = h->cfg.promote_k == 0 ? 512 : (h->cfg.promote_k < 0 ? 0 : h->cfg.promote_k);
+    c.cta_group = h->cfg.cta_group == 0 ? 1 : h->cfg.cta_group;
     if (h->cfg.split_k > 0) {
         c.split_k = h->cfg.split_k;
     } else {
@@ -324,7 +325,8 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
     const gemm_config_t& c = *cfg;
     if ((c.bn != 0 && c.bn != 128 && c.bn != 256) || (c.bk != 0 && c.bk != 32 && c.bk != 64) ||
         c.stages < 0 || c.stages > 8 || c.stages == 1 || c.split_k < 0 || c.split_k > 64 ||
-        c.raster_group < 0 || c.max_ctas < 0 || c.promote_k < -1 || c.reserved != 0 ||
+        c.raster_group < 0 || c.max_ctas < 0 || c.promote_k < -1 || c.cta_group < 0 ||
+        c.cta_group > 2 || (c.cta_group == 2 && c.bn == 128) ||
         c.wait_poll_limit < 0)
         return fail_arg(h, 2);
     h->cfg = c;

@@ -350,6 +350,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     p->flags = flags;
     p->cfg = gb300::handle_tc_config(h, nterms);
     p->cfg.split_k = 1;
+    p->cfg.cta_group = 1;  // grouped launches use one CTA per 128-row tile
 
     // workspace layout: per problem, A planes [planes][M][Kp] then B planes [planes][N][Kp]
     std::vector<HostProb> ps;
@@ -558,6 +559,7 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg
         cfg->raster_group = p->cfg.raster_group;
         cfg->max_ctas = p->cfg.max_ctas;
         cfg->promote_k = p->cfg.promote_k > 0 ? p->cfg.promote_k : -1;
+        cfg->cta_group = 1;
         cfg->wait_poll_limit = p->cfg.poll_limit;
     }
     if (tuned_ms) *tuned_ms = p->tuned_ms;

@@ -18,6 +18,7 @@ struct TcLaunch {
     int split_k = 1;         // K slices (>1: partial sums + reduce kernel)
     long long poll_limit = 0;  // 0 = default
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
+    int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)
 };
 
 // One operand of the tensor-core kernel: BF16, K-contiguous rows,

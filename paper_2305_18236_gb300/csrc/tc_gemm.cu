@@ -460,6 +460,309 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- CTA pairs
+// The same GEMM with CTA pairs (cluster of two, tcgen05 cta_group::2): a
+// pair owns a 256 x BN output tile; each CTA stages its 128 rows of A and
+// half (BN/2 rows) of B, so each SM moves half the B bytes of the one-CTA
+// kernel through shared memory, and the even CTA issues 256 x BN MMAs that
+// read both CTAs' tiles and write each CTA's 128 accumulator rows in its own
+// tensor memory.
+//
+// Synchronisation: each CTA's TMA signals its OWN full[s]; the odd CTA's
+// warp 1 forwards "my half of stage s landed" to the even CTA's peer_full[s]
+// with a remote arrive.  The even CTA's commits are multicast to both CTAs'
+// empty[s] / acc_full[b] / drain barriers; both CTAs' epilogue warps arrive on
+// the even CTA's acc_empty[b] (16 arrivals).  Keeping every TMA completion
+// local lets each producer drain its own copies on any exit path; a cluster
+// barrier before the tensor memory is freed keeps both CTAs alive until all
+// remote operations are done.
+template <int BN, int BK, int NTERMS>
+struct Shape2 {
+    static constexpr int PLANES = NTERMS == 1 ? 1 : 2;
+    static constexpr int BNH = BN / 2;  // B rows staged by each CTA
+    static constexpr int A_PLANE = kBM * BK * 2;
+    static constexpr int B_PLANE = BNH * BK * 2;
+    static constexpr int STAGE = PLANES * (A_PLANE + B_PLANE);
+    static constexpr int TMEM_COLS = 2 * BN;
+    static constexpr int ROW_BYTES = BK * 2;
+    static constexpr int BAR_BYTES = 1024;
+    static constexpr int STAGING = kEpiWarps * 32 * 33 * 4;
+    static_assert(B_PLANE % 1024 == 0, "B plane must keep swizzle atoms aligned");
+    static int smem_bytes(int stages) { return 1024 + stages * STAGE + BAR_BYTES + STAGING; }
+    static int max_stages() {
+        int s = (kMaxSmem - 1024 - BAR_BYTES - STAGING) / STAGE;
+        return s > 8 ? 8 : s;
+    }
+};
+
+template <int BN, int BK, int NTERMS, bool PROMOTE>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+    using S = Shape2<BN, BK, NTERMS>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~uintptr_t(1023));
+    const int stages = p.stages;
+    uint8_t* bar_area = smem + stages * S::STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);
+    uint64_t* empty = full + stages;
+    uint64_t* peer_full = empty + stages;
+    uint64_t* acc_full = peer_full + stages;  // [2]
+    uint64_t* acc_empty = acc_full + 2;       // [2]
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* staging = reinterpret_cast<float*>(bar_area + S::BAR_BYTES);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();  // 0: issues the MMAs
+    const int pair = blockIdx.x >> 1;
+    const int npairs = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&peer_full[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 2 * kEpiWarps);  // both CTAs' epilogue warps
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    __syncthreads();
+    cluster_sync();  // barriers initialised in both CTAs before any remote arrive
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, S::TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            const uint64_t pol = l2_policy_evict_last();
+            uint32_t filled = 0, fill_par = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+                for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait_bounded_cluster(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * S::STAGE;
+                    mbar_arrive_expect_tx(&full[s], S::STAGE);
+                    tma_load_3d(st, &tmA, &full[s], kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, 0,
+                                pol);
+                    tma_load_3d(st + S::PLANES * S::A_PLANE, &tmB, &full[s], kb * BK,
+                                ti.nt * BN + int(rank) * S::BNH, 0, pol);
+                    filled |= 1u << s;
+                    fill_par = (fill_par & ~(1u << s)) | (ph << s);
+                }
+            }
+            for (int s = 0; s < stages; ++s)
+                if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // -------------------------------------------- pair MMA issuer (even CTA)
+            constexpr uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN);
+            int it = 0, g = 0;
+            bool ok = true;
+            for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+                const int kb0 = ti.kb0, kb1 = ti.kb1;
+                const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
+                for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
+                    const int buf = g & 1;
+                    const uint32_t acc_ph = (g >> 1) & 1;
+                    if (!mbar_wait_bounded_cluster(&acc_empty[buf], acc_ph ^ 1, p.lim, abort_flag,
+                                                   p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + buf * BN;
+                    const int c1 = min(c0 + chunk, kb1);
+                    for (int kb = c0; kb < c1; ++kb, ++it) {
+                        const int s = it % stages;
+                        const uint32_t ph = (it / stages) & 1;
+                        if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err) ||
+                            !mbar_wait_bounded_cluster(&peer_full[s], ph, p.lim, abort_flag,
+                                                       p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
+                        const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
+                            if (NTERMS == 3) {
+                                const uint32_t a_lo = a_hi + S::A_PLANE;
+                                const uint32_t b_lo = b_hi + S::B_PLANE;
+                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
+                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
+                                               acc);
+                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                               make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc,
+                                               1u);
+                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
+                                               1u);
+                            } else {
+                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
+                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
+                                               acc);
+                            }
+                        }
+                        umma_commit_pair(&empty[s], 0x3);  // both CTAs may refill slot s
+                    }
+                    if (!ok) break;
+                    umma_commit_pair(&acc_full[buf], 0x3);
+                }
+            }
+            umma_commit_pair(drain, 0x3);  // both CTAs learn when every pair MMA is done
+            mbar_wait_drain_cluster(drain, 0, p.err);
+        } else if (lane == 0) {
+            // -------------------------------------------- forwarder (odd CTA)
+            const uint32_t leader_peer_full = mapa_shared(smem_u32(peer_full), 0);
+            int it = 0;
+            bool ok = true;
+            for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+                for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
+                    const int s = it % stages;
+                    const uint32_t ph = (it / stages) & 1;
+                    if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_remote(leader_peer_full + uint32_t(s) * 8u);
+                }
+            }
+            // the even CTA's MMAs read this CTA's tiles and write its TMEM
+            mbar_wait_drain_cluster(drain, 0, p.err);
+        }
+    } else {
+        // ------------------------------------------------ epilogue (both CTAs)
+        constexpr int COLS = BN / 2;
+        constexpr int PIECES = COLS / 32;
+        const int ew = warp & 3;
+        const int col_base = ((warp - 2) >> 2) * COLS;
+        float* stg = staging + (warp - 2) * 32 * 33;
+        float sum[PROMOTE ? COLS : 1];
+        const uint32_t leader_acc_empty = mapa_shared(smem_u32(acc_empty), 0);
+        int g = 0;
+        bool ok = true;
+#pragma unroll 1
+        for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+            const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+            const int kb0 = ti.kb0, kb1 = ti.kb1;
+            const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
+            const int row0 = ti.mt * 2 * kBM + int(rank) * kBM + ew * 32;
+            const int col0 = ti.nt * BN + col_base;
+#pragma unroll 1
+            for (int c0 = kb0; c0 < kb1; c0 += chunk, ++g) {
+                const int buf = g & 1;
+                const uint32_t acc_ph = (g >> 1) & 1;
+                int got = 0;
+                if (lane == 0)
+                    got = mbar_wait_bounded_cluster(&acc_full[buf], acc_ph, p.lim, abort_flag,
+                                                    p.err);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
+                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1)
+                    prefetch_c(get_epi<false>(0, ti.ks, p), row0, col0, COLS, lane);
+                if (PROMOTE) {
+                    if (c0 == kb0) {
+#pragma unroll
+                        for (int q = 0; q < 2 * PIECES; ++q) {
+                            uint32_t r[16];
+                            tmem_ld_32x32b_x16(taddr + q * 16, r);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) sum[q * 16 + j] = __uint_as_float(r[j]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 2 * PIECES; ++q) {
+                            uint32_t r[16];
+                            tmem_ld_32x32b_x16(taddr + q * 16, r);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) sum[q * 16 + j] += __uint_as_float(r[j]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0)
+                            mbar_arrive(&acc_empty[buf]);
+                        else
+                            mbar_arrive_remote(leader_acc_empty + uint32_t(buf) * 8u);
+                    }
+                    if (c0 + chunk >= kb1) {
+                        const EpiInfo e = get_epi<false>(0, ti.ks, p);
+#pragma unroll
+                        for (int q = 0; q < PIECES; ++q)
+                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int q = 0; q < PIECES; ++q) {
+                        uint32_t r[32];
+                        tmem_ld_32x32b_x32(taddr + q * 32, r);
+                        tmem_ld_wait();
+                        float v[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                        store_piece(v, stg, row0, col0 + q * 32, get_epi<false>(0, ti.ks, p), lane);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0)
+                            mbar_arrive(&acc_empty[buf]);
+                        else
+                            mbar_arrive_remote(leader_acc_empty + uint32_t(buf) * 8u);
+                    }
+                }
+            }
+        }
+    }
+
+    // ------------------------------------------------ teardown
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // no remote arrive or pair MMA may target a CTA that has left
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, S::TMEM_COLS);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -495,6 +798,52 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p, con
     if (ctas < 1) ctas = 1;
     kern<<<ctas, kThreads, smem, stream>>>(ta, tb, p);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <int BN, int BK, int NTERMS, bool PROMOTE>
+int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p,
+                        const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
+    using S = Shape2<BN, BK, NTERMS>;
+    int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
+    if (stages < 2) stages = 2;
+    p.stages = stages;
+    const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
+    const int smem = std::max(S::smem_bytes(stages), min_smem);
+    auto kern = tc_gemm_pair_kernel<BN, BK, NTERMS, PROMOTE>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return -4;
+    int pairs = num_sms / 2;
+    if (cfg.max_ctas > 0) pairs = std::min(pairs, std::max(1, cfg.max_ctas / 2));
+    pairs = std::max(1, std::min(pairs, p.num_tiles));
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(2 * pairs, 1, 1);
+    lc.blockDim = dim3(kThreads, 1, 1);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (cudaLaunchKernelEx(&lc, kern, ta, tb, p) != cudaSuccess) return -4;
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
+                  const CUtensorMap& tb, const TcParams& p, const TcLaunch& cfg, int num_sms,
+                  cudaStream_t s) {
+#define GB300_PAIR_CASE(BN_, BK_, NT_, PR_)                                                    \
+    if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
+        return launch_pair_variant<BN_, BK_, NT_, PR_>(ta, tb, p, cfg, num_sms, s);
+    GB300_PAIR_CASE(256, 32, 3, true)
+    GB300_PAIR_CASE(256, 64, 3, true)
+    GB300_PAIR_CASE(256, 32, 3, false)
+    GB300_PAIR_CASE(256, 64, 1, false)
+    GB300_PAIR_CASE(256, 32, 1, false)
+#undef GB300_PAIR_CASE
+    return -6;
 }
 
 template <bool GROUPED>
@@ -560,6 +909,8 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     if (M > (1ll << 31) - 256 || N > (1ll << 31) - 256 || K > (1ll << 31) - 256) return -6;
     const int bn = cfg.bn == 128 ? 128 : 256;
     const int bk = cfg.bk == 64 ? 64 : 32;
+    const bool pair = cfg.cta_group == 2 && bn == 256;
+    const int bm = pair ? 2 * kBM : kBM;  // output rows per tile (per CTA pair)
     TcParams p{};
     p.M = int(M);
     p.N = int(N);
@@ -568,7 +919,7 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     p.beta = beta;
     p.C = C;
     p.ldc = ldc;
-    p.num_m = int((M + kBM - 1) / kBM);
+    p.num_m = int((M + bm - 1) / bm);
     p.num_n = int((N + bn - 1) / bn);
     p.k_blocks = int((K + bk - 1) / bk);
     int split = std::max(1, cfg.split_k);
@@ -581,9 +932,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     p.num_tiles = p.num_m * p.num_n * split;
     fill_common(p, cfg, bk, nterms, err_word);
     CUtensorMap ta, tb;
-    if (!encode_operand(&ta, a, bk, kBM) || !encode_operand(&tb, b, bk, bn)) return -4;
+    if (!encode_operand(&ta, a, bk, kBM) || !encode_operand(&tb, b, bk, pair ? bn / 2 : bn))
+        return -4;
     const bool promote = nterms == 3 && cfg.promote_k > 0;
-    const int rc = dispatch<false>(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream);
+    const int rc = pair ? dispatch_pair(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream)
+                        : dispatch<false>(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream);
     if (rc != 0) return rc;
     int n = 1;
     if (split > 1) {

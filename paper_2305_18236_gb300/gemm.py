@@ -66,8 +66,8 @@ class Gemm:
 
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
-                   promote_k=0, wait_poll_limit=0):
-        cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, 0,
+                   promote_k=0, cta_group=0, wait_poll_limit=0):
+        cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
                             wait_poll_limit)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
 

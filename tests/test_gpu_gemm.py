@@ -213,3 +213,42 @@ def test_promotion_chunk_lengths(promote_k):
     bound = (chain + 2) * 2.0 ** -23 + (K // max(promote_k, 1) + 2) * 2.0 ** -24
     assert oracle.normwise_error(C, T64, D) <= bound
     h.close()
+
+
+@pytest.mark.parametrize("mode,bk,split", [("bf16", 64, 1), ("bf16", 32, 1), ("bf16x3", 32, 1),
+                                           ("bf16x3", 64, 1), ("bf16x3", 32, 3), ("bf16", 64, 2)])
+def test_cta_pair_kernel(mode, bk, split):
+    """The CTA-pair kernel (cluster of two, 256 x 256 tiles, each CTA staging
+    half of B) on ragged shapes, with and without split-K."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(bn=256, bk=bk, cta_group=2, split_k=split)
+    A, B, C0 = make_problem(700, 530, 1100, seed=81, beta=0.5)
+    check_mode(mode, A, B, 1.5, 0.5, C0, False, False, h=h)
+    Ai = inputs.integers((333, 999), 82)
+    Bi = inputs.integers((999, 777), 83)
+    Ci = inputs.integers((333, 777), 84)
+    C = run_mode(mode, Ai, Bi, 1.5, 0.5, Ci, False, False, h=h)
+    ref, _, _ = oracle.gemm(Ai, Bi, 1.5, 0.5, Ci)
+    assert np.array_equal(C.astype(np.float64), ref)
+    h.close()
+
+
+def test_cta_pair_timeout_path():
+    """The pair kernel's bounded waits expire cleanly too (one-poll limit)."""
+    import torch
+
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(bn=256, cta_group=2, wait_poll_limit=1)
+    A, B, _ = make_problem(1024, 1024, 2048, seed=85)
+    C = torch.zeros((1024, 1024), device="cuda")
+    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, mode="bf16x3", h=h)
+    assert h.sync() == _lib.GEMM_ERR_TIMEOUT
+    h.reset_config()
+    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, mode="bf16x3", h=h)
+    assert h.sync() == _lib.GEMM_OK
+    h.close()
