@@ -65,6 +65,7 @@ struct TcParams {
     const CUtensorMap* maps;
     const int* tile_prob;  // problem index of every tile
     int count;
+    int c_tma;  // epilogue writes through the C tensor map (beta == 0 or split-K partials)
 };
 
 template <int BN, int BK, int NTERMS>
@@ -227,10 +228,44 @@ __device__ __forceinline__ void prefetch_c(const EpiInfo& ti, int row0, int col0
     }
 }
 
+// The same 32 x 32 piece stored by TMA: the warp writes alpha * v into its
+// 4 KB slab in the 128-byte-swizzled layout of the C tensor map (row l of the
+// piece is lane l; its 16-byte chunk c sits at chunk c ^ (l % 8)), then one
+// lane issues a bulk tensor store to (col0, row0, z).  TMA clips the parts
+// of the box outside C.  Before rewriting the slab the lane waits until its
+// previous store has finished reading it.
+__device__ __forceinline__ void store_piece_tma(const float* v, float* slab, int row0, int col0,
+                                                int z, float alpha, const CUtensorMap* map,
+                                                int lane) {
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    uint8_t* row = reinterpret_cast<uint8_t*>(slab) + lane * 128;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4*>(row + ((c ^ (lane & 7)) << 4)) =
+            make_float4(alpha * v[4 * c], alpha * v[4 * c + 1], alpha * v[4 * c + 2],
+                        alpha * v[4 * c + 3]);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        tma_store_3d(map, slab, col0, row0, z);
+        bulk_commit_group();
+    }
+}
+
+// The one-CTA kernel.  GROUPED: tiles of many problems (per-tile problem
+// lookup, tensor maps in device memory).  PROMOTE: the K range of a tile is
+// cut into chunks of p.chunk_kb k-blocks; each chunk is accumulated in TMEM
+// from zero and then added, in FP32 with round-to-nearest, into registers of
+// the epilogue warps.  The tensor core's own FP32 accumulation rounds toward
+// zero, so its error grows with the number of MMAs summed into one
+// accumulator; short chunks bound that growth and the register sums carry
+// the rest of K with ordinary FP32 rounding.  Without PROMOTE a tile is one
+// chunk.
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcParams p) {
+                   const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     using S = Shape<BN, BK, NTERMS>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -372,6 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ew = warp & 3;
         const int col_base = ((warp - 2) >> 2) * COLS;
         float* stg = staging + (warp - 2) * 32 * 33;
+        float* slab = staging + (warp - 2) * 1024;  // 4 KB, 1024-byte aligned (TMA store)
         float sum[PROMOTE ? COLS : 1];
         int g = 0;
         bool ok = true;
@@ -426,9 +462,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);  // TMEM free before the stores
                     if (c0 + chunk >= kb1) {
                         const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
+                        if (p.c_tma) {
 #pragma unroll
-                        for (int q = 0; q < PIECES; ++q) {
-                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
+                            for (int q = 0; q < PIECES; ++q)
+                                store_piece_tma(&sum[q * 32], slab, row0, col0 + q * 32, ti.ks,
+                                                e.alpha, &tmC, lane);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < PIECES; ++q)
+                                store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
                         }
                     }
                 } else {
@@ -440,8 +482,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                        store_piece(v, stg, row0, col0 + q * 32,
-                                    get_epi<GROUPED>(ti.prob, ti.ks, p), lane);
+                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
+                        if (p.c_tma)
+                            store_piece_tma(v, slab, row0, col0 + q * 32, ti.ks, e.alpha, &tmC,
+                                            lane);
+                        else
+                            store_piece(v, stg, row0, col0 + q * 32, e, lane);
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -452,6 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // ------------------------------------------------ teardown
+    if (warp >= 2 && lane == 0) bulk_wait_all();  // TMA stores of C finished
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -498,7 +545,8 @@ struct Shape2 {
 template <int BN, int BK, int NTERMS, bool PROMOTE>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
-                        const __grid_constant__ CUtensorMap tmB, const TcParams p) {
+                        const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     using S = Shape2<BN, BK, NTERMS>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -667,6 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ew = warp & 3;
         const int col_base = ((warp - 2) >> 2) * COLS;
         float* stg = staging + (warp - 2) * 32 * 33;
+        float* slab = staging + (warp - 2) * 1024;  // 4 KB, 1024-byte aligned (TMA store)
         float sum[PROMOTE ? COLS : 1];
         const uint32_t leader_acc_empty = mapa_shared(smem_u32(acc_empty), 0);
         int g = 0;
@@ -725,9 +774,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (c0 + chunk >= kb1) {
                         const EpiInfo e = get_epi<false>(0, ti.ks, p);
+                        if (p.c_tma) {
 #pragma unroll
-                        for (int q = 0; q < PIECES; ++q)
-                            store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
+                            for (int q = 0; q < PIECES; ++q)
+                                store_piece_tma(&sum[q * 32], slab, row0, col0 + q * 32, ti.ks,
+                                                e.alpha, &tmC, lane);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < PIECES; ++q)
+                                store_piece(&sum[q * 32], stg, row0, col0 + q * 32, e, lane);
+                        }
                     }
                 } else {
 #pragma unroll 1
@@ -738,7 +794,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                        store_piece(v, stg, row0, col0 + q * 32, get_epi<false>(0, ti.ks, p), lane);
+                        const EpiInfo e = get_epi<false>(0, ti.ks, p);
+                        if (p.c_tma)
+                            store_piece_tma(v, slab, row0, col0 + q * 32, ti.ks, e.alpha, &tmC,
+                                            lane);
+                        else
+                            store_piece(v, stg, row0, col0 + q * 32, e, lane);
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -754,6 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // ------------------------------------------------ teardown
+    if (warp >= 2 && lane == 0) bulk_wait_all();  // TMA stores of C finished
     tc_fence_before();
     __syncthreads();
     cluster_sync();  // no remote arrive or pair MMA may target a CTA that has left
@@ -779,8 +841,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
-int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p, const TcLaunch& cfg,
-                   int num_sms, cudaStream_t stream) {
+int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
+                   TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
     using S = Shape<BN, BK, NTERMS>;
     int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
     if (stages < 2) stages = 2;
@@ -796,13 +858,13 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p, con
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
     if (ctas < 1) ctas = 1;
-    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, p);
+    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, tc, p);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 template <int BN, int BK, int NTERMS, bool PROMOTE>
-int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p,
-                        const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
+int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
+                        TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
     using S = Shape2<BN, BK, NTERMS>;
     int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
     if (stages < 2) stages = 2;
@@ -827,16 +889,16 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, TcParams p
     attr[0].val.clusterDim.z = 1;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    if (cudaLaunchKernelEx(&lc, kern, ta, tb, p) != cudaSuccess) return -4;
+    if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
 int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
-                  const CUtensorMap& tb, const TcParams& p, const TcLaunch& cfg, int num_sms,
-                  cudaStream_t s) {
+                  const CUtensorMap& tb, const CUtensorMap& tc, const TcParams& p,
+                  const TcLaunch& cfg, int num_sms, cudaStream_t s) {
 #define GB300_PAIR_CASE(BN_, BK_, NT_, PR_)                                                    \
     if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
-        return launch_pair_variant<BN_, BK_, NT_, PR_>(ta, tb, p, cfg, num_sms, s);
+        return launch_pair_variant<BN_, BK_, NT_, PR_>(ta, tb, tc, p, cfg, num_sms, s);
     GB300_PAIR_CASE(256, 32, 3, true)
     GB300_PAIR_CASE(256, 64, 3, true)
     GB300_PAIR_CASE(256, 32, 3, false)
@@ -848,11 +910,11 @@ int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& t
 
 template <bool GROUPED>
 int dispatch(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
-             const CUtensorMap& tb, const TcParams& p, const TcLaunch& cfg, int num_sms,
-             cudaStream_t s) {
+             const CUtensorMap& tb, const CUtensorMap& tc, const TcParams& p, const TcLaunch& cfg,
+             int num_sms, cudaStream_t s) {
 #define GB300_TC_CASE(BN_, BK_, NT_, PR_)                                                      \
     if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
-        return launch_variant<BN_, BK_, NT_, PR_, GROUPED>(ta, tb, p, cfg, num_sms, s);
+        return launch_variant<BN_, BK_, NT_, PR_, GROUPED>(ta, tb, tc, p, cfg, num_sms, s);
     GB300_TC_CASE(256, 32, 3, true)
     GB300_TC_CASE(256, 64, 3, true)
     GB300_TC_CASE(128, 32, 3, true)
@@ -867,6 +929,20 @@ int dispatch(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
     GB300_TC_CASE(128, 64, 1, false)
 #undef GB300_TC_CASE
     return -6;
+}
+
+// 3-D (column, row, slab) FP32 map of C (or of the split-K partial slabs)
+// with the 32 x 32 box and 128-byte swizzle the TMA-store epilogue writes.
+bool encode_output(CUtensorMap* map, float* base, int64_t M, int64_t N, int64_t ld, int slabs) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {cuuint64_t(N), cuuint64_t(M), cuuint64_t(slabs)};
+    cuuint64_t strides[2] = {cuuint64_t(ld) * 4, cuuint64_t(ld) * cuuint64_t(M) * 4};
+    cuuint32_t box[3] = {32, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void fill_common(TcParams& p, const TcLaunch& cfg, int bk, int nterms, int* err_word) {
@@ -931,12 +1007,19 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     if (split > 1 && partial == nullptr) return -3;
     p.num_tiles = p.num_m * p.num_n * split;
     fill_common(p, cfg, bk, nterms, err_word);
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tc{};
     if (!encode_operand(&ta, a, bk, kBM) || !encode_operand(&tb, b, bk, pair ? bn / 2 : bn))
         return -4;
+    // beta == 0 (or split-K partials): store C tiles with TMA when C allows it
+    if (split > 1) {
+        p.c_tma = (N % 4 == 0) && encode_output(&tc, partial, M, N, N, split);
+    } else if (beta == 0.0f && (reinterpret_cast<uintptr_t>(C) & 15) == 0 && ldc % 4 == 0) {
+        p.c_tma = encode_output(&tc, C, M, N, ldc, 1);
+    }
     const bool promote = nterms == 3 && cfg.promote_k > 0;
-    const int rc = pair ? dispatch_pair(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream)
-                        : dispatch<false>(nterms, promote, bn, bk, ta, tb, p, cfg, num_sms, stream);
+    const int rc = pair ? dispatch_pair(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream)
+                        : dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
+                                          stream);
     if (rc != 0) return rc;
     int n = 1;
     if (split > 1) {
@@ -964,7 +1047,8 @@ int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev
     fill_common(p, cfg, bk, nterms, err_word);
     CUtensorMap unused{};  // grouped kernels read their maps from dev_maps
     const bool promote = nterms == 3 && cfg.promote_k > 0;
-    return dispatch<true>(nterms, promote, bn, bk, unused, unused, p, cfg, num_sms, stream);
+    return dispatch<true>(nterms, promote, bn, bk, unused, unused, unused, p, cfg, num_sms,
+                          stream);
 }
 
 }  // namespace gb300

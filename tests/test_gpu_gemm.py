@@ -252,3 +252,41 @@ def test_cta_pair_timeout_path():
     g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, mode="bf16x3", h=h)
     assert h.sync() == _lib.GEMM_OK
     h.close()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (129, 33, 70), (300, 516, 200), (257, 1000, 64),
+                                   (640, 260, 2048)])
+def test_beta_zero_tma_store(mode, M, N, K):
+    """beta == 0: the epilogue stores C tiles with TMA (clipped at ragged
+    edges); C padding columns beyond N stay untouched."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    A = inputs.integers((M, K), 91)
+    B = inputs.integers((K, N), 92)
+    Cb = torch.full((M, N + 4), -7.0, device="cuda")  # ldc = N + 4 keeps 16-byte rows
+    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=Cb[:, :N], alpha=1.5,
+             mode=mode)
+    torch.cuda.synchronize()
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.0)
+    out = Cb.cpu().numpy()
+    assert np.array_equal(out[:, :N].astype(np.float64), ref)
+    assert np.all(out[:, N:] == -7.0)
+
+
+def test_beta_zero_unaligned_c_falls_back():
+    """An ld that breaks 16-byte row alignment takes the ordinary store path."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 200, 300, 96
+    A = inputs.integers((M, K), 93)
+    B = inputs.integers((K, N), 94)
+    Cb = torch.zeros((M, N + 1), device="cuda")
+    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=Cb[:, :N], mode="bf16x3")
+    torch.cuda.synchronize()
+    ref, _, _ = oracle.gemm(A, B)
+    assert np.array_equal(Cb[:, :N].cpu().numpy().astype(np.float64), ref)
