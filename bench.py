@@ -53,6 +53,25 @@ def parse():
     return p.parse_args()
 
 
+def load_traffic():
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    summary, or None once the kernel sources differ from the captured ones."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "tc_gemm_bf16x3_8192_dram_traffic.md")
+    src = [os.path.join(ROOT, "paper_2305_18236_gb300", "csrc", f) for f in ("tc_gemm.cu", "ptx.cuh")]
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines()
+                  if line.startswith(("traffic_bytes_per_launch: ", "source_sha256: ")))
+    if fields.get("source_sha256", "").strip() != h:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -326,7 +345,7 @@ def run_ours(args):
                 "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "%s dense BF16 (cuBLAS, sustained)" % peak_src}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = load_traffic() if (mode == "bf16x3" and n == 8192) else None
     roof["kernel_ms"] = kernel_ms
 
     # FP32 SIMT comparison on the same workload
