@@ -164,11 +164,13 @@ gemm_status_t gemm_split_bf16(gemm_handle_t handle, gemm_op_t trans, int64_t row
                               int64_t ldo, void *stream);
 
 /* gemm() on HOST buffers: copies A, B (and C when beta != 0) to device
- * buffers the handle owns (grown with cudaMalloc on demand), runs gemm() on
- * `stream`, copies C back and synchronises the stream.  Pinned host memory
- * gives asynchronous copies; pageable memory works but is slower.  Also
- * reports a kernel's bounded-wait expiry (GEMM_ERR_TIMEOUT).  Positions as
- * for gemm(). */
+ * buffers the handle owns (grown with cudaMalloc on demand), computes, copies
+ * C back and synchronises `stream`.  B is copied (and split) first; then up
+ * to four row blocks of op(A) and C are each copied in, multiplied and copied
+ * out on two streams the handle owns, so the copies of one block overlap the
+ * GEMM of its neighbours.  Pinned host memory gives asynchronous, overlapped
+ * copies; pageable memory works but is slower.  Also reports a kernel's
+ * bounded-wait expiry (GEMM_ERR_TIMEOUT).  Positions as for gemm(). */
 gemm_status_t gemm_from_host(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                              int64_t M, int64_t N, int64_t K,
                              float alpha, const float *A, int64_t lda,

@@ -30,6 +30,8 @@ struct gemm_context {
     float* hB = nullptr;
     float* hC = nullptr;
     size_t hA_bytes = 0, hB_bytes = 0, hC_bytes = 0;
+    cudaStream_t pipe[2] = {nullptr, nullptr};  // gemm_from_host row-block streams
+    cudaEvent_t pipe_ev[3] = {nullptr, nullptr, nullptr};
     // benchmark hook: event pairs around main kernels
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;  // 2 per recorded launch
@@ -311,6 +313,10 @@ gemm_status_t gemm_destroy(gemm_handle_t h) {
     if (h->hA) cudaFree(h->hA);
     if (h->hB) cudaFree(h->hB);
     if (h->hC) cudaFree(h->hC);
+    for (cudaStream_t st : h->pipe)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : h->pipe_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
     return GEMM_OK;
 }
@@ -449,31 +455,108 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3)
         return fail_arg(h, 15);
     if (M == 0 || N == 0) return GEMM_OK;
+    if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const bool reads_ab = K > 0 && alpha != 0.0f;
-    const int64_t ar = transA ? K : M, ac = transA ? M : K;
-    const int64_t br = transB ? N : K, bc = transB ? K : N;
-    if (reads_ab) {
-        if ((st = grow(&h->hA, &h->hA_bytes, size_t(ar) * lda * 4)) != GEMM_OK) return st;
-        if ((st = grow(&h->hB, &h->hB_bytes, size_t(br) * ldb * 4)) != GEMM_OK) return st;
-        if (cudaMemcpy2DAsync(h->hA, lda * 4, A, lda * 4, ac * 4, ar, cudaMemcpyHostToDevice, s) !=
-                cudaSuccess ||
-            cudaMemcpy2DAsync(h->hB, ldb * 4, B, ldb * 4, bc * 4, br, cudaMemcpyHostToDevice, s) !=
+    if ((st = grow(&h->hC, &h->hC_bytes, size_t(M) * ldc * 4)) != GEMM_OK) return st;
+    if (K == 0 || alpha == 0.0f) {  // C <- beta C: no operand copies
+        if (beta != 0.0f && cudaMemcpy2DAsync(h->hC, ldc * 4, C, ldc * 4, N * 4, M,
+                                              cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        if (gb300::launch_scale_c(M, N, beta, h->hC, ldc, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(C, ldc * 4, h->hC, ldc * 4, N * 4, M, cudaMemcpyDeviceToHost, s) !=
                 cudaSuccess)
             return GEMM_ERR_CUDA;
+        st = gemm_sync(h, stream);
+        h->last_launches = 1;
+        return st;
     }
-    if ((st = grow(&h->hC, &h->hC_bytes, size_t(M) * ldc * 4)) != GEMM_OK) return st;
-    if (beta != 0.0f &&
-        cudaMemcpy2DAsync(h->hC, ldc * 4, C, ldc * 4, N * 4, M, cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-        return GEMM_ERR_CUDA;
-    st = run_gemm(h, transA, transB, M, N, K, alpha, h->hA, lda, h->hB, ldb, beta, h->hC, ldc, mode,
-                  s);
-    if (st != GEMM_OK) return st;
-    if (cudaMemcpy2DAsync(C, ldc * 4, h->hC, ldc * 4, N * 4, M, cudaMemcpyDeviceToHost, s) !=
+    const int64_t ar = transA ? K : M;
+    const int64_t br = transB ? N : K, bc = transB ? K : N;
+    if ((st = grow(&h->hA, &h->hA_bytes, size_t(ar) * lda * 4)) != GEMM_OK) return st;
+    if ((st = grow(&h->hB, &h->hB_bytes, size_t(br) * ldb * 4)) != GEMM_OK) return st;
+    for (int i = 0; i < 2; ++i)
+        if (!h->pipe[i] && cudaStreamCreateWithFlags(&h->pipe[i], cudaStreamNonBlocking) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+    for (int i = 0; i < 3; ++i)
+        if (!h->pipe_ev[i] && cudaEventCreateWithFlags(&h->pipe_ev[i], cudaEventDisableTiming) !=
+                                  cudaSuccess)
+            return GEMM_ERR_CUDA;
+
+    // Row blocks of op(A) and C: block i is copied in, computed and copied
+    // out on stream pipe[i % 2], so the copies of one block overlap the
+    // GEMM of its neighbours.  B is copied (and split) once, first.
+    const int nb = int(std::min<int64_t>(4, std::max<int64_t>(1, M / 1024)));
+    const int64_t rb = ((M + nb - 1) / nb + 127) / 128 * 128;
+    const bool tc = mode != GEMM_MODE_F32_SIMT;
+    const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
+    const int planes = nterms == 3 ? 2 : 1;
+    TcLaunch cfg = plan_tc(h, nterms, rb, N, K);
+    cfg.split_k = 1;
+    WsPlan w{};
+    uint8_t* ws = nullptr;
+    if (tc) {
+        w = plan_ws(planes, true, true, M, N, K, cfg);
+        if ((st = get_ws(h, w.total, &ws)) != GEMM_OK) return st;
+    }
+    uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
+    uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
+    int launches = 0;
+    if (cudaMemcpy2DAsync(h->hB, ldb * 4, B, ldb * 4, bc * 4, br, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return GEMM_ERR_CUDA;
-    const int launches = h->last_launches;
+    if (tc) {
+        if (gb300::launch_split_bf16(!transB, N, K, h->hB, ldb, b_hi,
+                                     planes > 1 ? b_hi + N * w.kp : nullptr, w.kp, s) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        ++launches;
+    }
+    if (cudaEventRecord(h->pipe_ev[0], s) != cudaSuccess) return GEMM_ERR_CUDA;
+    for (int i = 0; i < nb; ++i) {
+        const int64_t r0 = i * rb;
+        if (r0 >= M) break;
+        const int64_t rows = std::min(rb, M - r0);
+        cudaStream_t si = h->pipe[i & 1];
+        if (cudaStreamWaitEvent(si, h->pipe_ev[0], 0) != cudaSuccess) return GEMM_ERR_CUDA;
+        // rows r0.. of op(A): stored rows of A, or stored columns when transposed
+        const size_t aoff = transA ? size_t(r0) : size_t(r0) * lda;
+        const cudaError_t ce =
+            transA ? cudaMemcpy2DAsync(h->hA + aoff, lda * 4, A + aoff, lda * 4, rows * 4, K,
+                                       cudaMemcpyHostToDevice, si)
+                   : cudaMemcpy2DAsync(h->hA + aoff, lda * 4, A + aoff, lda * 4, K * 4, rows,
+                                       cudaMemcpyHostToDevice, si);
+        if (ce != cudaSuccess) return GEMM_ERR_CUDA;
+        float* cblk = h->hC + size_t(r0) * ldc;
+        if (beta != 0.0f && cudaMemcpy2DAsync(cblk, ldc * 4, C + size_t(r0) * ldc, ldc * 4, N * 4,
+                                              rows, cudaMemcpyHostToDevice, si) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        if (tc) {
+            uint16_t* ablk = a_hi + r0 * w.kp;
+            if (gb300::launch_split_bf16(transA, rows, K, h->hA + aoff, lda, ablk,
+                                         planes > 1 ? ablk + M * w.kp : nullptr, w.kp, si) !=
+                cudaSuccess)
+                return GEMM_ERR_CUDA;
+            TcOperand oa{ablk, rows, K, w.kp, M * w.kp, planes};
+            TcOperand ob{b_hi, N, K, w.kp, N * w.kp, planes};
+            int n = 0;
+            const int rc = gb300::launch_tc_gemm(oa, ob, nterms, rows, N, K, alpha, beta, cblk, ldc,
+                                                 nullptr, cfg, h->err_word, h->num_sms, si, &n);
+            if (rc != 0) return static_cast<gemm_status_t>(rc);
+            launches += 1 + n;
+        } else {
+            if (gb300::launch_simt_f32(transA, transB, rows, N, K, alpha, h->hA + aoff, lda, h->hB,
+                                       ldb, beta, cblk, ldc, si) != cudaSuccess)
+                return GEMM_ERR_CUDA;
+            ++launches;
+        }
+        if (cudaMemcpy2DAsync(C + size_t(r0) * ldc, ldc * 4, cblk, ldc * 4, N * 4, rows,
+                              cudaMemcpyDeviceToHost, si) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+    }
+    // join both block streams back into the caller's stream
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventRecord(h->pipe_ev[1 + i], h->pipe[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, h->pipe_ev[1 + i], 0) != cudaSuccess)
+            return GEMM_ERR_CUDA;
     st = gemm_sync(h, stream);
     h->last_launches = launches;
     return st;

@@ -104,6 +104,26 @@ def test_from_host(mode):
     assert oracle.normwise_error(tC.numpy(), C64, D) <= tol_exact(mode, 250)
 
 
+@pytest.mark.parametrize("mode,tA,tB", [("bf16x3", False, False), ("bf16x3", True, True),
+                                         ("f32_simt", True, False), ("bf16", False, True)])
+def test_from_host_pipelined_blocks(mode, tA, tB):
+    """Large M: gemm_from_host splits op(A) and C into row blocks on two
+    streams; sampled rows of every block against the oracle."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 4500, 700, 600
+    A, B, C0 = make_problem(M, N, K, tA, tB, seed=95, beta=0.5)
+    tAh = torch.from_numpy(A).pin_memory()
+    tBh = torch.from_numpy(B).pin_memory()
+    tC = torch.from_numpy(C0.copy()).pin_memory()
+    g.gemm_from_host(tAh, tBh, C=tC, alpha=1.5, beta=0.5, transA=tA, transB=tB, mode=mode)
+    rows = np.linspace(0, M - 1, 40).astype(np.int64)
+    C64, D, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB, rows=rows)
+    assert oracle.normwise_error(tC.numpy()[rows], C64, D) <= tol_exact(mode, K)
+
+
 @pytest.mark.parametrize("tA,tB", [(False, False), (True, True), (False, True), (True, False)])
 def test_backward_matches_oracle_gradient(tA, tB):
     """dA = dC op(B)^T and dB = op(A)^T dC, against the oracle's FP64 GEMMs
