@@ -352,11 +352,22 @@ def run_ours(args):
     compare = None
     if not args.no_compare and mode != "f32_simt":
         simt_steps = max(3, min(10, args.steps))
-        ms_s = time_steps(lambda: step(g.MODES["f32_simt"]), simt_steps, 2, world, stream)
+        for _ in range(2):
+            step(g.MODES["f32_simt"])
+        torch.cuda.synchronize()
+        simt_clocks = ClockSampler(uuid)
+        simt_clocks.start()
+        ms_s = time_steps(lambda: step(g.MODES["f32_simt"]), simt_steps, 0, world, stream)
+        sclk = simt_clocks.stop()
         ms_s = max_over_ranks(ms_s, world)
         simt = world * flops * simt_steps / (ms_s / 1e3) / 1e12
+        sms = props.multi_processor_count
         compare = {"f32_simt_tflops": simt, "speedup_vs_f32_simt": value / simt,
-                   "f32_simt_ms_per_step": ms_s / simt_steps}
+                   "f32_simt_ms_per_step": ms_s / simt_steps, "f32_simt_clocks": sclk}
+        if sclk and sclk.get("sm_mhz"):
+            # FP32 peak at the clock the SIMT kernel actually ran at
+            peak_at_clock = sms * 128 * 2 * sclk["sm_mhz"] * 1e6 / 1e12
+            compare["f32_simt_frac_of_peak_at_clock"] = simt / world / peak_at_clock
 
     # end to end through the public API with pinned host buffers
     hA = torch.from_numpy(A).pin_memory()

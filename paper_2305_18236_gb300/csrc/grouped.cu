@@ -42,7 +42,9 @@ struct gemm_grouped_plan_s {
     gb300::GroupedProblem* d_probs = nullptr;
     CUtensorMap* d_maps = nullptr;
     int* d_tile_prob = nullptr;
-    int* d_tile_job = nullptr;
+    int* d_tile_job = nullptr;    // tiles of direct (non-transposed) jobs
+    int* d_tile_job_t = nullptr;  // tiles of transposed jobs
+    int split_tiles_t = 0;
     int njobs = 0, split_tiles = 0, nprobs = 0, total_tiles = 0;
     // problems handled by a plain scale (K == 0 or alpha == 0)
     struct Scale {
@@ -237,6 +239,7 @@ void free_plan(gemm_grouped_plan_s* p) {
     if (p->d_maps) cudaFree(p->d_maps);
     if (p->d_tile_prob) cudaFree(p->d_tile_prob);
     if (p->d_tile_job) cudaFree(p->d_tile_job);
+    if (p->d_tile_job_t) cudaFree(p->d_tile_job_t);
     delete p;
 }
 
@@ -286,7 +289,9 @@ gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
         if (gb300::launch_scale_c(sc.M, sc.N, sc.beta, sc.C, sc.ldc, s) != cudaSuccess)
             return GEMM_ERR_CUDA;
     if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
-                                    p->num_sms, s) != cudaSuccess)
+                                    p->num_sms, s) != cudaSuccess ||
+        gb300::launch_split_grouped_t(p->d_jobs, p->d_tile_job_t, p->njobs, p->split_tiles_t,
+                                      p->num_sms, s) != cudaSuccess)
         return GEMM_ERR_CUDA;
     const int rc = gb300::launch_tc_grouped(p->nterms, p->cfg, p->d_probs, p->d_maps,
                                             p->d_tile_prob, p->nprobs, p->total_tiles,
@@ -355,7 +360,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     // workspace layout: per problem, A planes [planes][M][Kp] then B planes [planes][N][Kp]
     std::vector<HostProb> ps;
     std::vector<SplitJob> jobs;
-    std::vector<int> tile_job;
+    std::vector<int> tile_job, tile_job_t;
+    int tiles_t = 0;
     std::vector<size_t> a_off, b_off;
     size_t ws = 0;
     for (int i = 0; i < count; ++i) {
@@ -396,10 +402,14 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         ja.trans = q.transA;
         ja.x_vec = ((reinterpret_cast<uintptr_t>(q.A) & 15) == 0) && (q.lda % 4 == 0);
         ja.tiles_r = int((q.M + 63) / 64);
-        ja.tile_start = tiles;
-        tiles += ja.tiles_r * int((q.K + 63) / 64);
-        tile_job.insert(tile_job.end(), size_t(ja.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
-        jobs.push_back(ja);
+        {
+            int& cnt = ja.trans ? tiles_t : tiles;
+            std::vector<int>& map = ja.trans ? tile_job_t : tile_job;
+            ja.tile_start = cnt;
+            cnt += ja.tiles_r * int((q.K + 63) / 64);
+            map.insert(map.end(), size_t(ja.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
+            jobs.push_back(ja);
+        }
         SplitJob jb{};
         jb.src = q.B;
         jb.ldx = q.ldb;
@@ -411,10 +421,14 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         jb.trans = !q.transB;  // op(B)^T is N x K
         jb.x_vec = ((reinterpret_cast<uintptr_t>(q.B) & 15) == 0) && (q.ldb % 4 == 0);
         jb.tiles_r = int((q.N + 63) / 64);
-        jb.tile_start = tiles;
-        tiles += jb.tiles_r * int((q.K + 63) / 64);
-        tile_job.insert(tile_job.end(), size_t(jb.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
-        jobs.push_back(jb);
+        {
+            int& cnt = jb.trans ? tiles_t : tiles;
+            std::vector<int>& map = jb.trans ? tile_job_t : tile_job;
+            jb.tile_start = cnt;
+            cnt += jb.tiles_r * int((q.K + 63) / 64);
+            map.insert(map.end(), size_t(jb.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
+            jobs.push_back(jb);
+        }
         HostProb hq;
         hq.a = TcOperand{ah, q.M, q.K, kp, q.M * kp, planes};
         hq.b = TcOperand{bh, q.N, q.K, kp, q.N * kp, planes};
@@ -429,9 +443,11 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     }
     p->njobs = int(jobs.size());
     p->split_tiles = tiles;
+    p->split_tiles_t = tiles_t;
     p->nprobs = int(ps.size());
     gemm_status_t st = upload(&p->d_jobs, jobs, s);
     if (st == GEMM_OK) st = upload(&p->d_tile_job, tile_job, s);
+    if (st == GEMM_OK) st = upload(&p->d_tile_job_t, tile_job_t, s);
     if (st != GEMM_OK) {
         free_plan(p);
         return st;
@@ -448,7 +464,9 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         } else {
             // operands must be split before the candidates can be timed
             if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
-                                            p->num_sms, s) != cudaSuccess) {
+                                            p->num_sms, s) != cudaSuccess ||
+                gb300::launch_split_grouped_t(p->d_jobs, p->d_tile_job_t, p->njobs,
+                                              p->split_tiles_t, p->num_sms, s) != cudaSuccess) {
                 free_plan(p);
                 return GEMM_ERR_CUDA;
             }
@@ -515,7 +533,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         free_plan(p);
         return st;
     }
-    p->launches = int(p->scales.size()) + (p->njobs > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0);
+    p->launches = int(p->scales.size()) + (p->split_tiles > 0 ? 1 : 0) +
+                  (p->split_tiles_t > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0);
     *plan = p;
     return GEMM_OK;
 }

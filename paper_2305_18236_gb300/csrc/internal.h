@@ -102,6 +102,11 @@ struct SplitJob {
 cudaError_t launch_split_grouped(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
                                  int total_tiles, int num_sms, cudaStream_t stream);
 
+// The same for a table whose tile map lists only transposed jobs, with a
+// double-buffered shared tile (asynchronous copies of the next tile in flight).
+cudaError_t launch_split_grouped_t(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
+                                   int total_tiles, int num_sms, cudaStream_t stream);
+
 // Y = op(X) for BF16 X (a pure re-layout), rows x cols, row stride ldo.
 cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,
                              int64_t ldx, uint16_t* out, int64_t ldo, cudaStream_t stream);

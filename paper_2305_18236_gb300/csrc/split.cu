@@ -305,7 +305,104 @@ __global__ void __launch_bounds__(256, 8) split_grouped_kernel(const SplitJob* _
     }
 }
 
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the 4-byte asynchronous copies of transposed tile t (X rows c0..+63,
+// columns r0..+63) into `buf`; out-of-range elements are zero-filled.
+__device__ __forceinline__ void load_transposed_tile(const SplitJob* __restrict__ jobs,
+                                                     const int* __restrict__ tile_job, int t,
+                                                     float (*buf)[65], int tid) {
+    const SplitJob& j = jobs[__ldg(&tile_job[t])];
+    const int local = t - j.tile_start;
+    const int64_t r0 = int64_t(local % j.tiles_r) * 64;
+    const int64_t c0 = int64_t(local / j.tiles_r) * 64;
+#pragma unroll
+    for (int pass = 0; pass < 16; ++pass) {
+        const int i = pass * 4 + (tid >> 6);
+        const int jj = tid & 63;
+        const int64_t xr = c0 + i, xc = r0 + jj;
+        if (xr < j.cols && xc < j.rows)
+            cp_async4(&buf[i][jj], j.src + xr * j.ldx + xc);
+        else
+            buf[i][jj] = 0.0f;
+    }
+    cp_async_commit();
+}
+
+// Grouped split of transposed jobs only (Y = X^T): the shared tile is double
+// buffered and the next tile's copies are in flight while the current tile
+// is converted and stored, so each block keeps two tiles of reads pending.
+__global__ void __launch_bounds__(256, 6) split_grouped_t_kernel(const SplitJob* __restrict__ jobs,
+                                                              const int* __restrict__ tile_job,
+                                                              int total_tiles) {
+    __shared__ float tile[2][64][65];
+    const int tid = threadIdx.x;
+    int t = blockIdx.x;
+    if (t < total_tiles) load_transposed_tile(jobs, tile_job, t, tile[0], tid);
+    for (int k = 0; t < total_tiles; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int tn = t + gridDim.x;
+        if (tn < total_tiles) {
+            load_transposed_tile(jobs, tile_job, tn, tile[b ^ 1], tid);
+            cp_async_wait<1>();  // tile t has landed; tile tn may still be in flight
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const SplitJob& j = jobs[__ldg(&tile_job[t])];
+        const int local = t - j.tile_start;
+        const int64_t r0 = int64_t(local % j.tiles_r) * 64;
+        const int64_t c0 = int64_t(local / j.tiles_r) * 64;
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+            const int rr = pass * 32 + (tid >> 3);
+            const int cc = (tid & 7) * 8;
+            const int64_t yr = r0 + rr, yc = c0 + cc;
+            if (yr < j.rows && yc < j.cols) {
+                uint16_t h[8], l[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) split1(tile[b][cc + q][rr], h[q], l[q]);
+                uint16_t* dh = j.hi + yr * j.ldo + yc;
+                uint16_t* dl = j.lo ? j.lo + yr * j.ldo + yc : nullptr;
+                if (yc + 8 <= j.cols) {
+                    *reinterpret_cast<uint4*>(dh) = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]),
+                                                               pack2(h[4], h[5]), pack2(h[6], h[7]));
+                    if (dl)
+                        *reinterpret_cast<uint4*>(dl) = make_uint4(
+                            pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+                } else {
+                    for (int q = 0; q < 8 && yc + q < j.cols; ++q) {
+                        dh[q] = h[q];
+                        if (dl) dl[q] = l[q];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // tile[b] is refilled by the copies issued next iteration
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_split_grouped_t(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
+                                   int total_tiles, int num_sms, cudaStream_t stream) {
+    if (njobs <= 0 || total_tiles <= 0) return cudaSuccess;
+    const int grid = std::max(1, std::min(total_tiles, num_sms * 12));
+    split_grouped_t_kernel<<<grid, 256, 0, stream>>>(dev_jobs, dev_tile_job, total_tiles);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_split_grouped(const SplitJob* dev_jobs, const int* dev_tile_job, int njobs,
                                  int total_tiles, int num_sms, cudaStream_t stream) {
