@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-compare", action="store_true", help="skip the FP32 SIMT comparison")
     p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--operand-layout", default="as_stored", choices=["as_stored", "k_major"],
+                   help="as_stored: operands stored K x rows are split without transposing and "
+                        "read as MN-major tiles; k_major: every operand made K-contiguous first")
     p.add_argument("--workload", default="square", choices=["square", "rect", "grouped", "chain"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
                         "grouped: 512 uneven problems; chain: Y = X W forward + backward")
@@ -174,12 +177,15 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def square_config(n, mode, world):
+def square_config(n, mode, world, layout=None):
     """The workload description shared by both arms of the headline line."""
-    return {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
-                        % (n, n, n),
-            "mode": mode, "M": n, "N": n, "K": n, "parallelism": "replicas x%d" % world,
-            "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush"}
+    cfg = {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
+                       % (n, n, n),
+           "mode": mode, "M": n, "N": n, "K": n, "parallelism": "replicas x%d" % world,
+           "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush"}
+    if layout is not None:
+        cfg["operand_layout"] = layout
+    return cfg
 
 
 def make_inputs(n):
@@ -296,6 +302,7 @@ def run_ours(args):
     dB = torch.from_numpy(B).to(dev)
     dC = torch.from_numpy(C0).to(dev)
     h = g.Gemm(dev)
+    h.set_config(operand_layout=args.operand_layout)
     stream = torch.cuda.current_stream(dev)
     mode = args.mode
     mcode = g.MODES[mode]
@@ -414,7 +421,7 @@ def run_ours(args):
         "dtype": {"bf16x3": "bf16x3 (bf16 hi/lo products, f32 accumulate)",
                   "bf16": "bf16 (f32 accumulate)", "f32_simt": "f32"}[mode],
         "data": "synthetic",
-        "config": square_config(n, mode, world),
+        "config": square_config(n, mode, world, args.operand_layout),
         "launches_per_step": launches_per_step,
         "roofline": roof,
         "gpu_launches": launches_per_step * args.steps,
@@ -465,30 +472,39 @@ def run_rect(args):
     torch.cuda.set_device(0)
     peaks, src = load_peaks()
     stream = torch.cuda.current_stream()
+    h = g.Gemm()
+    h.set_config(operand_layout=args.operand_layout)
     out = []
     for (M, N, K) in [(16384, 4096, 1024), (4096, 16384, 4096), (128, 8192, 8192),
                       (8192, 8192, 64)]:
         gen = torch.Generator(device="cuda").manual_seed(SEED)
         A = (torch.randn((M, K), device="cuda", generator=gen) / np.sqrt(K)).to(torch.bfloat16)
-        B = (torch.randn((N, K), device="cuda", generator=gen) / np.sqrt(K)).to(torch.bfloat16)
+        B = (torch.randn((K, N), device="cuda", generator=gen) / np.sqrt(K)).to(torch.bfloat16)
+        Bt = B.t().contiguous()
         C = torch.empty((M, N), device="cuda")
-        # B stored N x K (transB): both operands K-contiguous, read in place by TMA
-        ms = _events_ms(lambda: g.matmul_bf16(A, B, C=C, transB=True), args.steps, args.warmup,
-                        stream)
+        # NN: B stored K x N is read in place as MN-major tiles (as_stored), or
+        # packed K-contiguous first (k_major); NT (B stored N x K) for comparison
+        ms = _events_ms(lambda: g.matmul_bf16(A, B, C=C, h=h), args.steps, args.warmup, stream)
+        launches = h.last_launch_count()
+        ms_nt = _events_ms(lambda: g.matmul_bf16(A, Bt, C=C, transB=True, h=h), args.steps,
+                           args.warmup, stream)
         flops = 2.0 * M * N * K
         nbytes = 2.0 * (M * K + N * K) + 4.0 * M * N
         out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
                     "gbs": nbytes / ms / 1e6,
                     "frac_tensor": flops / ms / 1e9 / peaks["bf16_tflops"],
                     "frac_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"],
-                    "launches": g.handle().last_launch_count()})
+                    "launches": launches, "nt_ms": ms_nt})
+        del A, B, Bt, C
+    h.close()
     tot_flops = sum(2.0 * r["M"] * r["N"] * r["K"] for r in out)
     tot_ms = sum(r["ms"] for r in out)
     print(json.dumps({"metric": "rectangular BF16-input GEMM TFLOP/s (sum over 4 shapes)",
                       "value": tot_flops / tot_ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                       "dtype": "bf16 in, f32 accumulate/out", "data": "synthetic",
-                      "config": {"workload": "bf16 NT shapes, N(0,1/sqrt(K))"},
+                      "config": {"workload": "bf16 NN shapes, N(0,1/sqrt(K))",
+                                 "operand_layout": args.operand_layout},
                       "shapes": out, "peaks_source": src}), flush=True)
 
 
@@ -515,12 +531,14 @@ def run_grouped(args):
                           C=torch.empty((M, N), device="cuda")))
     flops = sum(2.0 * M * N * K for (M, N, K) in shapes)
     stream = torch.cuda.Stream()
+    h = g.Gemm()
+    h.set_config(operand_layout=args.operand_layout)
     res = {}
     with torch.cuda.stream(stream):
         for name, kw in [("fixed_eager", dict()), ("fixed_graph", dict(graph=True)),
                          ("tuned_graph", dict(autotune=True, graph=True))]:
             t0 = time.perf_counter()
-            plan = g.GroupedPlan(probs, mode=args.mode, **kw)
+            plan = g.GroupedPlan(probs, mode=args.mode, h=h, **kw)
             create_s = time.perf_counter() - t0
             ms = _events_ms(plan.run, args.steps, args.warmup, stream)
             res[name] = {"ms": ms, "tflops": flops / ms / 1e9, "config": plan.config(),
@@ -532,7 +550,8 @@ def run_grouped(args):
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
                       "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
                       "config": {"workload": "512 problems, M,N,K ~ 32*U{2..64}, FP32 U[-1,1]",
-                                 "flops_per_step": flops},
+                                 "flops_per_step": flops,
+                                 "operand_layout": args.operand_layout},
                       "variants": res}), flush=True)
 
 

@@ -87,7 +87,16 @@ typedef struct gemm_context *gemm_handle_t;
  *    SMs shares a 256-row tile, each staging half of B; bn must be 256);
  *    0 = library choice.
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
- *    the device error word and exits cleanly (0 = default, about seconds). */
+ *    the device error word and exits cleanly (0 = default, about seconds).
+ *  operand_layout: GEMM_LAYOUT_AS_STORED (0, default): each operand reaches
+ *    the tensor cores in its stored orientation -- A stored K x M (transA ==
+ *    T) and B stored K x N (transB == N) are split without transposing and
+ *    read as MN-major tiles, and gemm_bf16 reads every operand in place;
+ *    GEMM_LAYOUT_K_MAJOR (1): every operand is made K-contiguous first (a
+ *    transposing split, or a pack pass in gemm_bf16).  CTA pairs always use
+ *    K-major tiles. */
+typedef enum { GEMM_LAYOUT_AS_STORED = 0, GEMM_LAYOUT_K_MAJOR = 1 } gemm_layout_t;
+
 typedef struct {
     int32_t bn;
     int32_t bk;
@@ -98,6 +107,8 @@ typedef struct {
     int32_t promote_k;
     int32_t cta_group;
     int64_t wait_poll_limit;
+    int32_t operand_layout;
+    int32_t reserved; /* must be 0 */
 } gemm_config_t;
 
 /* Create a handle bound to the CURRENT CUDA device.  Allocates a 256-byte
@@ -142,11 +153,13 @@ gemm_status_t gemm(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                    gemm_mode_t mode, void *stream);
 
 /* C <- alpha * op(A) op(B) + beta * C with BF16 A and B (uint16_t bit
- * patterns), FP32 C, tensor cores with FP32 accumulation.  Operands that
- * are already K-contiguous (transA == N, transB == T) are read in place and
- * need a 16-byte aligned base and ld % 8 == 0 (else GEMM_ERR_ALIGN); the
- * others are first packed K-contiguous into workspace (Algorithm 1's
- * pack step).  Argument positions as for gemm() (no mode; 15 is stream). */
+ * patterns), FP32 C, tensor cores with FP32 accumulation.  Operands are read
+ * in place by TMA in their stored orientation (K-contiguous, or MN-contiguous
+ * for A stored K x M and B stored K x N) and need a 16-byte aligned base and
+ * ld % 8 == 0 (else GEMM_ERR_ALIGN).  With operand_layout ==
+ * GEMM_LAYOUT_K_MAJOR (or CTA pairs) the MN-contiguous operands are instead
+ * packed K-contiguous into workspace first (Algorithm 1's pack step) and may
+ * have any ld.  Argument positions as for gemm() (no mode; 15 is stream). */
 gemm_status_t gemm_bf16(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                         int64_t M, int64_t N, int64_t K,
                         float alpha, const uint16_t *A, int64_t lda,

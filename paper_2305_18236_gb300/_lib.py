@@ -15,6 +15,9 @@ MODE_F32_SIMT, MODE_BF16, MODE_BF16X3 = 0, 1, 2
 MODES = {"f32_simt": MODE_F32_SIMT, "simt": MODE_F32_SIMT, "bf16": MODE_BF16,
          "bf16x3": MODE_BF16X3}
 
+LAYOUT_AS_STORED, LAYOUT_K_MAJOR = 0, 1
+LAYOUTS = {"as_stored": LAYOUT_AS_STORED, "k_major": LAYOUT_K_MAJOR}
+
 GEMM_OK = 0
 GEMM_ERR_ARG = -1
 GEMM_ERR_ALIGN = -2
@@ -32,7 +35,8 @@ _i32, _i64, _f32, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, cty
 class gemm_config_t(ctypes.Structure):
     _fields_ = [("bn", _i32), ("bk", _i32), ("stages", _i32), ("split_k", _i32),
                 ("raster_group", _i32), ("max_ctas", _i32), ("promote_k", _i32),
-                ("cta_group", _i32), ("wait_poll_limit", _i64)]
+                ("cta_group", _i32), ("wait_poll_limit", _i64), ("operand_layout", _i32),
+                ("reserved", _i32)]
 
 
 class gemm_problem_t(ctypes.Structure):

@@ -46,7 +46,6 @@ using gb300::TcOperand;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-int64_t round8(int64_t k) { return (k + 7) / 8 * 8; }
 
 gemm_status_t fail_arg(gemm_context* h, int pos) {
     if (h) h->last_err_arg = pos;
@@ -66,6 +65,8 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
     c.poll_limit = h->cfg.wait_poll_limit;
     c.promote_k = h->cfg.promote_k == 0 ? 512 : (h->cfg.promote_k < 0 ? 0 : h->cfg.promote_k);
     c.cta_group = h->cfg.cta_group == 0 ? 1 : h->cfg.cta_group;
+    // CTA pairs stage K-major tiles only
+    c.kmajor = (h->cfg.operand_layout == GEMM_LAYOUT_K_MAJOR || c.cta_group == 2) ? 1 : 0;
     if (h->cfg.split_k > 0) {
         c.split_k = h->cfg.split_k;
     } else {
@@ -82,26 +83,58 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
 
 struct WsPlan {
     size_t a_off = 0, b_off = 0, p_off = 0, total = 0;
-    int64_t kp = 0;
     int planes = 1;
     int split = 1;
 };
 
-// Workspace of a tensor-core call: packed A (planes x M x Kp BF16), packed B
-// (planes x N x Kp BF16), split-K partials (split x M x N FP32).
-WsPlan plan_ws(int planes, bool pack_a, bool pack_b, int64_t M, int64_t N, int64_t K,
+// How one operand reaches the tensor cores after the split / pack pass.  An
+// operand stored K x rows (A with transA == T, B with transB == N) keeps
+// that orientation (MN-major tiles, a plain non-transposing pass) unless the
+// launch wants every operand K-major; the others become op(X) as rows x K.
+struct OpPlan {
+    bool stored_k_rows;  // stored K x rows
+    bool mn;             // packed MN-major
+    gb300::PackedLayout lay;
+};
+
+OpPlan plan_op(int64_t rows, int64_t K, bool stored_k_rows, const TcLaunch& c) {
+    OpPlan o;
+    o.stored_k_rows = stored_k_rows;
+    o.mn = stored_k_rows && !c.kmajor;
+    o.lay = gb300::packed_layout(rows, K, o.mn);
+    return o;
+}
+
+// Split op(X) (rows x K) into hi (and lo, `planes` == 2) planes at `hi` in the
+// operand's packed layout.
+cudaError_t split_op(const OpPlan& o, int64_t rows, int64_t K, const float* X, int64_t ldx,
+                     uint16_t* hi, int planes, cudaStream_t s) {
+    uint16_t* lo = planes > 1 ? hi + o.lay.plane : nullptr;
+    if (o.mn) return gb300::launch_split_bf16(0, K, rows, X, ldx, hi, lo, o.lay.ld, s);
+    return gb300::launch_split_bf16(o.stored_k_rows ? 1 : 0, rows, K, X, ldx, hi, lo, o.lay.ld, s);
+}
+
+TcOperand operand_of(const OpPlan& o, const uint16_t* hi, int64_t rows, int64_t K, int planes) {
+    TcOperand t{hi, rows, K, o.lay.ld, o.lay.plane, planes};
+    t.mn_major = o.mn ? 1 : 0;
+    return t;
+}
+
+// Workspace of a tensor-core call: packed A and packed B (planes x the
+// operand's packed plane, BF16; plane size 0 = not packed), split-K partials
+// (split x M x N FP32).
+WsPlan plan_ws(int planes, int64_t a_plane, int64_t b_plane, int64_t M, int64_t N, int64_t K,
                const TcLaunch& c) {
     WsPlan w;
-    w.kp = round8(K);
     w.planes = planes;
     size_t off = 0;
-    if (pack_a) {
+    if (a_plane > 0) {
         w.a_off = off;
-        off += align_up(size_t(planes) * M * w.kp * 2);
+        off += align_up(size_t(planes) * a_plane * 2);
     }
-    if (pack_b) {
+    if (b_plane > 0) {
         w.b_off = off;
-        off += align_up(size_t(planes) * N * w.kp * 2);
+        off += align_up(size_t(planes) * b_plane * 2);
     }
     const int64_t kblocks = (K + c.bk - 1) / c.bk;
     int split = std::max(1, std::min<int>(c.split_k, int(std::max<int64_t>(kblocks, 1))));
@@ -216,22 +249,20 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
     const TcLaunch cfg = plan_tc(h, nterms, M, N, K);
-    const WsPlan w = plan_ws(planes, true, true, M, N, K, cfg);
+    // op(A) is M x K and op(B)^T is N x K; each is split in its stored orientation
+    const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
+    const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
+    const WsPlan w = plan_ws(planes, pa.lay.plane, pb.lay.plane, M, N, K, cfg);
     uint8_t* ws;
     gemm_status_t st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
     uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
     uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
-    const int64_t a_plane = M * w.kp, b_plane = N * w.kp;
-    // pack/split op(A) as M x K and op(B)^T as N x K, both K-contiguous
-    if (gb300::launch_split_bf16(transA, M, K, A, lda, a_hi, planes > 1 ? a_hi + a_plane : nullptr,
-                                 w.kp, s) != cudaSuccess)
+    if (split_op(pa, M, K, A, lda, a_hi, planes, s) != cudaSuccess ||
+        split_op(pb, N, K, B, ldb, b_hi, planes, s) != cudaSuccess)
         return GEMM_ERR_CUDA;
-    if (gb300::launch_split_bf16(!transB, N, K, B, ldb, b_hi, planes > 1 ? b_hi + b_plane : nullptr,
-                                 w.kp, s) != cudaSuccess)
-        return GEMM_ERR_CUDA;
-    TcOperand oa{a_hi, M, K, w.kp, a_plane, planes};
-    TcOperand ob{b_hi, N, K, w.kp, b_plane, planes};
+    const TcOperand oa = operand_of(pa, a_hi, M, K, planes);
+    const TcOperand ob = operand_of(pb, b_hi, N, K, planes);
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
     float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
@@ -270,8 +301,12 @@ int* handle_err_word(gemm_handle_t h) { return h->err_word; }
 void handle_set_err_arg(gemm_handle_t h, int pos) { h->last_err_arg = pos; }
 void handle_set_launches(gemm_handle_t h, int n) { h->last_launches = n; }
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
-    // tile choice of the handle's configuration (problem-size independent parts)
-    return plan_tc(h, nterms, 1 << 20, 1 << 20, 1);
+    // tile choice of the handle's configuration (problem-size independent
+    // parts) for grouped launches, which use one CTA per 128-row tile
+    TcLaunch c = plan_tc(h, nterms, 1 << 20, 1 << 20, 1);
+    c.cta_group = 1;
+    c.kmajor = h->cfg.operand_layout == GEMM_LAYOUT_K_MAJOR ? 1 : 0;
+    return c;
 }
 }  // namespace gb300
 
@@ -333,7 +368,9 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         c.stages < 0 || c.stages > 8 || c.stages == 1 || c.split_k < 0 || c.split_k > 64 ||
         c.raster_group < 0 || c.max_ctas < 0 || c.promote_k < -1 || c.cta_group < 0 ||
         c.cta_group > 2 || (c.cta_group == 2 && c.bn == 128) ||
-        c.wait_poll_limit < 0)
+        c.wait_poll_limit < 0 ||
+        (c.operand_layout != GEMM_LAYOUT_AS_STORED && c.operand_layout != GEMM_LAYOUT_K_MAJOR) ||
+        c.reserved != 0)
         return fail_arg(h, 2);
     h->cfg = c;
     return GEMM_OK;
@@ -344,11 +381,14 @@ size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, 
     if (!h || M < 0 || N < 0 || K < 0) return 0;
     if (M == 0 || N == 0 || K == 0 || mode == GEMM_MODE_F32_SIMT) return 0;
     if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
-    (void)transA;
-    (void)transB;
+    if ((transA != GEMM_OP_N && transA != GEMM_OP_T) || (transB != GEMM_OP_N && transB != GEMM_OP_T))
+        return 0;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const TcLaunch c = plan_tc(h, nterms, M, N, K);
-    return plan_ws(nterms == 3 ? 2 : 1, true, true, M, N, K, c).total;
+    const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
+    const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, c);
+    // gemm() splits both operands; gemm_bf16 needs at most as much (packs only)
+    return plan_ws(nterms == 3 ? 2 : 1, pa.lay.plane, pb.lay.plane, M, N, K, c).total;
 }
 
 gemm_status_t gemm_set_workspace(gemm_handle_t h, void* ws, size_t bytes) {
@@ -384,29 +424,37 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
         return status_of(gb300::launch_scale_c(M, N, beta, C, ldc, s));
     }
     if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
-    // K-contiguous operands are read in place by TMA; the rest are packed.
-    const bool pack_a = transA == GEMM_OP_T;
-    const bool pack_b = transB == GEMM_OP_N;
+    // Operands are read in place by TMA in their stored orientation: K-major
+    // (A stored M x K, B stored N x K) or MN-major (A stored K x M, B stored
+    // K x N).  Only when the launch wants every operand K-major are the
+    // MN-contiguous ones packed first.
+    const TcLaunch cfg = plan_tc(h, 1, M, N, K);
+    const bool a_kr = transA == GEMM_OP_T, b_kr = transB == GEMM_OP_N;  // stored K x rows
+    const bool pack_a = a_kr && cfg.kmajor;
+    const bool pack_b = b_kr && cfg.kmajor;
     if (!pack_a && ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 8))) return GEMM_ERR_ALIGN;
     if (!pack_b && ((reinterpret_cast<uintptr_t>(B) & 15) || (ldb % 8))) return GEMM_ERR_ALIGN;
-    const TcLaunch cfg = plan_tc(h, 1, M, N, K);
-    const WsPlan w = plan_ws(1, pack_a, pack_b, M, N, K, cfg);
+    const gb300::PackedLayout la = gb300::packed_layout(M, K, false);
+    const gb300::PackedLayout lb = gb300::packed_layout(N, K, false);
+    const WsPlan w = plan_ws(1, pack_a ? la.plane : 0, pack_b ? lb.plane : 0, M, N, K, cfg);
     uint8_t* ws;
     st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
     int launches = 0;
-    TcOperand oa{A, M, K, lda, M * lda, 1};
-    TcOperand ob{B, N, K, ldb, N * ldb, 1};
+    TcOperand oa{A, M, K, lda, 0, 1};
+    oa.mn_major = a_kr ? 1 : 0;
+    TcOperand ob{B, N, K, ldb, 0, 1};
+    ob.mn_major = b_kr ? 1 : 0;
     if (pack_a) {
         uint16_t* pa = reinterpret_cast<uint16_t*>(ws + w.a_off);
-        if (gb300::launch_pack_bf16(1, M, K, A, lda, pa, w.kp, s) != cudaSuccess) return GEMM_ERR_CUDA;
-        oa = TcOperand{pa, M, K, w.kp, M * w.kp, 1};
+        if (gb300::launch_pack_bf16(1, M, K, A, lda, pa, la.ld, s) != cudaSuccess) return GEMM_ERR_CUDA;
+        oa = TcOperand{pa, M, K, la.ld, la.plane, 1};
         ++launches;
     }
     if (pack_b) {
         uint16_t* pb = reinterpret_cast<uint16_t*>(ws + w.b_off);
-        if (gb300::launch_pack_bf16(1, N, K, B, ldb, pb, w.kp, s) != cudaSuccess) return GEMM_ERR_CUDA;
-        ob = TcOperand{pb, N, K, w.kp, N * w.kp, 1};
+        if (gb300::launch_pack_bf16(1, N, K, B, ldb, pb, lb.ld, s) != cudaSuccess) return GEMM_ERR_CUDA;
+        ob = TcOperand{pb, N, K, lb.ld, lb.plane, 1};
         ++launches;
     }
     TcLaunch c2 = cfg;
@@ -492,10 +540,12 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     const int planes = nterms == 3 ? 2 : 1;
     TcLaunch cfg = plan_tc(h, nterms, rb, N, K);
     cfg.split_k = 1;
+    const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
+    const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
     WsPlan w{};
     uint8_t* ws = nullptr;
     if (tc) {
-        w = plan_ws(planes, true, true, M, N, K, cfg);
+        w = plan_ws(planes, pa.lay.plane, pb.lay.plane, M, N, K, cfg);
         if ((st = get_ws(h, w.total, &ws)) != GEMM_OK) return st;
     }
     uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
@@ -505,9 +555,7 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
         cudaSuccess)
         return GEMM_ERR_CUDA;
     if (tc) {
-        if (gb300::launch_split_bf16(!transB, N, K, h->hB, ldb, b_hi,
-                                     planes > 1 ? b_hi + N * w.kp : nullptr, w.kp, s) != cudaSuccess)
-            return GEMM_ERR_CUDA;
+        if (split_op(pb, N, K, h->hB, ldb, b_hi, planes, s) != cudaSuccess) return GEMM_ERR_CUDA;
         ++launches;
     }
     if (cudaEventRecord(h->pipe_ev[0], s) != cudaSuccess) return GEMM_ERR_CUDA;
@@ -530,13 +578,13 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
                                               rows, cudaMemcpyHostToDevice, si) != cudaSuccess)
             return GEMM_ERR_CUDA;
         if (tc) {
-            uint16_t* ablk = a_hi + r0 * w.kp;
-            if (gb300::launch_split_bf16(transA, rows, K, h->hA + aoff, lda, ablk,
-                                         planes > 1 ? ablk + M * w.kp : nullptr, w.kp, si) !=
-                cudaSuccess)
+            // the block's rows inside the packed A: packed rows (K-major) or
+            // columns (MN-major; r0 is a multiple of 128, so 16-byte aligned)
+            uint16_t* ablk = a_hi + (pa.mn ? r0 : r0 * pa.lay.ld);
+            if (split_op(pa, rows, K, h->hA + aoff, lda, ablk, planes, si) != cudaSuccess)
                 return GEMM_ERR_CUDA;
-            TcOperand oa{ablk, rows, K, w.kp, M * w.kp, planes};
-            TcOperand ob{b_hi, N, K, w.kp, N * w.kp, planes};
+            const TcOperand oa = operand_of(pa, ablk, rows, K, planes);
+            const TcOperand ob = operand_of(pb, b_hi, N, K, planes);
             int n = 0;
             const int rc = gb300::launch_tc_gemm(oa, ob, nterms, rows, N, K, alpha, beta, cblk, ldc,
                                                  nullptr, cfg, h->err_word, h->num_sms, si, &n);

@@ -99,6 +99,7 @@ int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
         g.tile_start = tiles;
         g.alpha = q.alpha;
         g.beta = q.beta;
+        g.major = (q.a.mn_major ? 1 : 0) | (q.b.mn_major ? 2 : 0);
         tiles += g.num_m * g.num_n;
         tile_prob.insert(tile_prob.end(), size_t(g.num_m) * g.num_n, int(i));
         probs.push_back(g);
@@ -162,7 +163,8 @@ std::string shape_key(int device_sms, int nterms, const std::vector<HostProb>& p
     // order-independent signature: count and a hash of the sorted shapes
     std::vector<uint64_t> v;
     for (const HostProb& q : ps)
-        v.push_back((uint64_t(q.M) << 42) ^ (uint64_t(q.N) << 21) ^ uint64_t(q.K));
+        v.push_back((uint64_t(q.M) << 42) ^ (uint64_t(q.N) << 21) ^ uint64_t(q.K) ^
+                    (uint64_t(q.a.mn_major + 2 * q.b.mn_major) << 62));
     std::sort(v.begin(), v.end());
     uint64_t h = 1469598103934665603ull;
     for (uint64_t x : v) {
@@ -357,7 +359,12 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     p->cfg.split_k = 1;
     p->cfg.cta_group = 1;  // grouped launches use one CTA per 128-row tile
 
-    // workspace layout: per problem, A planes [planes][M][Kp] then B planes [planes][N][Kp]
+    // Workspace layout: per problem, the hi (and lo) planes of A, then of B.
+    // An operand stored K x rows (A with transA, B without transB) keeps that
+    // orientation (MN-major tiles, split without transposing) unless the
+    // handle asks for K-major operands.
+    auto a_mn = [&](const gemm_problem_t& q) { return q.transA != 0 && !p->cfg.kmajor; };
+    auto b_mn = [&](const gemm_problem_t& q) { return q.transB == 0 && !p->cfg.kmajor; };
     std::vector<HostProb> ps;
     std::vector<SplitJob> jobs;
     std::vector<int> tile_job, tile_job_t;
@@ -371,11 +378,10 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->scales.push_back({q.M, q.N, q.ldc, q.beta, q.C});
             continue;
         }
-        const int64_t kp = (q.K + 7) / 8 * 8;
         a_off.push_back(ws);
-        ws += round256(size_t(planes) * q.M * kp * 2);
+        ws += round256(size_t(planes) * gb300::packed_layout(q.M, q.K, a_mn(q)).plane * 2);
         b_off.push_back(ws);
-        ws += round256(size_t(planes) * q.N * kp * 2);
+        ws += round256(size_t(planes) * gb300::packed_layout(q.N, q.K, b_mn(q)).plane * 2);
     }
     if (ws > 0 && cudaMalloc(reinterpret_cast<void**>(&p->ws), ws) != cudaSuccess) {
         cudaGetLastError();
@@ -387,51 +393,39 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     for (int i = 0; i < count; ++i) {
         const gemm_problem_t& q = hp[i];
         if (q.M == 0 || q.N == 0 || q.K == 0 || q.alpha == 0.0f) continue;
-        const int64_t kp = (q.K + 7) / 8 * 8;
         uint16_t* ah = reinterpret_cast<uint16_t*>(p->ws + a_off[idx]);
         uint16_t* bh = reinterpret_cast<uint16_t*>(p->ws + b_off[idx]);
         ++idx;
-        SplitJob ja{};
-        ja.src = q.A;
-        ja.ldx = q.lda;
-        ja.hi = ah;
-        ja.lo = planes > 1 ? ah + q.M * kp : nullptr;
-        ja.ldo = kp;
-        ja.rows = int(q.M);
-        ja.cols = int(q.K);
-        ja.trans = q.transA;
-        ja.x_vec = ((reinterpret_cast<uintptr_t>(q.A) & 15) == 0) && (q.lda % 4 == 0);
-        ja.tiles_r = int((q.M + 63) / 64);
-        {
-            int& cnt = ja.trans ? tiles_t : tiles;
-            std::vector<int>& map = ja.trans ? tile_job_t : tile_job;
-            ja.tile_start = cnt;
-            cnt += ja.tiles_r * int((q.K + 63) / 64);
-            map.insert(map.end(), size_t(ja.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
-            jobs.push_back(ja);
-        }
-        SplitJob jb{};
-        jb.src = q.B;
-        jb.ldx = q.ldb;
-        jb.hi = bh;
-        jb.lo = planes > 1 ? bh + q.N * kp : nullptr;
-        jb.ldo = kp;
-        jb.rows = int(q.N);
-        jb.cols = int(q.K);
-        jb.trans = !q.transB;  // op(B)^T is N x K
-        jb.x_vec = ((reinterpret_cast<uintptr_t>(q.B) & 15) == 0) && (q.ldb % 4 == 0);
-        jb.tiles_r = int((q.N + 63) / 64);
-        {
-            int& cnt = jb.trans ? tiles_t : tiles;
-            std::vector<int>& map = jb.trans ? tile_job_t : tile_job;
-            jb.tile_start = cnt;
-            cnt += jb.tiles_r * int((q.K + 63) / 64);
-            map.insert(map.end(), size_t(jb.tiles_r) * ((q.K + 63) / 64), int(jobs.size()));
-            jobs.push_back(jb);
-        }
+        // One split job per operand: op(X) as rows x K (K-major, transposing
+        // when X is stored K x rows) or X as stored, K x rows (MN-major).
+        auto add_job = [&](const float* src, int64_t ldx, uint16_t* hi, int64_t rows,
+                           bool stored_k_rows, bool mn) {
+            const gb300::PackedLayout lay = gb300::packed_layout(rows, q.K, mn);
+            SplitJob j{};
+            j.src = src;
+            j.ldx = ldx;
+            j.hi = hi;
+            j.lo = planes > 1 ? hi + lay.plane : nullptr;
+            j.ldo = lay.ld;
+            j.rows = int(mn ? q.K : rows);
+            j.cols = int(mn ? rows : q.K);
+            j.trans = (stored_k_rows && !mn) ? 1 : 0;
+            j.x_vec = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && (ldx % 4 == 0);
+            j.tiles_r = (j.rows + 63) / 64;
+            const int tiles_c = (j.cols + 63) / 64;
+            int& cnt = j.trans ? tiles_t : tiles;
+            std::vector<int>& map = j.trans ? tile_job_t : tile_job;
+            j.tile_start = cnt;
+            cnt += j.tiles_r * tiles_c;
+            map.insert(map.end(), size_t(j.tiles_r) * tiles_c, int(jobs.size()));
+            jobs.push_back(j);
+            TcOperand op{hi, rows, q.K, lay.ld, lay.plane, planes};
+            op.mn_major = mn ? 1 : 0;
+            return op;
+        };
         HostProb hq;
-        hq.a = TcOperand{ah, q.M, q.K, kp, q.M * kp, planes};
-        hq.b = TcOperand{bh, q.N, q.K, kp, q.N * kp, planes};
+        hq.a = add_job(q.A, q.lda, ah, q.M, q.transA != 0, a_mn(q));
+        hq.b = add_job(q.B, q.ldb, bh, q.N, q.transB == 0, b_mn(q));
         hq.M = q.M;
         hq.N = q.N;
         hq.K = q.K;
@@ -580,6 +574,8 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg
         cfg->promote_k = p->cfg.promote_k > 0 ? p->cfg.promote_k : -1;
         cfg->cta_group = 1;
         cfg->wait_poll_limit = p->cfg.poll_limit;
+        cfg->operand_layout = p->cfg.kmajor ? GEMM_LAYOUT_K_MAJOR : GEMM_LAYOUT_AS_STORED;
+        cfg->reserved = 0;
     }
     if (tuned_ms) *tuned_ms = p->tuned_ms;
     return GEMM_OK;

@@ -19,12 +19,15 @@ struct TcLaunch {
     long long poll_limit = 0;  // 0 = default
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
     int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)
+    int kmajor = 0;          // 1: every operand K-major (transposing split / pack)
 };
 
-// One operand of the tensor-core kernel: BF16, K-contiguous rows,
-// `planes` stacked planes (1: hi only; 2: hi then lo), `rows` x `k`
-// elements per plane, row stride `ld` elements, plane stride `plane_ld`
-// elements.
+// One operand of the tensor-core kernel: BF16, `planes` stacked planes
+// (1: hi only; 2: hi then lo) `plane_ld` elements apart, each holding the
+// operand's `rows` (M for A, N for B) x `k` elements.  K-major (mn_major 0):
+// one stored row per operand row, K contiguous, row stride `ld`.  MN-major
+// (mn_major 1): one stored row per K index, the operand rows contiguous,
+// row stride `ld` (the layout of A stored K x M, or of B stored K x N).
 struct TcOperand {
     const uint16_t* base;
     int64_t rows;
@@ -32,7 +35,20 @@ struct TcOperand {
     int64_t ld;
     int64_t plane_ld;
     int planes;
+    int mn_major = 0;
 };
+
+// Row stride and plane size (elements) of an operand written by the split
+// or pack pass: K-major rows x round8(k), or MN-major k x round8(rows), so
+// that every stored row starts on a 16-byte boundary.
+struct PackedLayout {
+    int64_t ld;
+    int64_t plane;
+};
+inline PackedLayout packed_layout(int64_t rows, int64_t k, bool mn_major) {
+    const int64_t ld = ((mn_major ? rows : k) + 7) / 8 * 8;
+    return PackedLayout{ld, (mn_major ? k : rows) * ld};
+}
 
 // One problem of a grouped tensor-core launch, as the kernel reads it from
 // device memory.  tile_start is the index of the problem's first output
@@ -44,11 +60,13 @@ struct GroupedProblem {
     int num_m, num_n, k_blocks;
     int tile_start;
     float alpha, beta;
-    int pad;
+    int major;  // bit 0: A MN-major, bit 1: B MN-major (TcOperand::mn_major)
 };
 
-// Encode the 3-D (k, row, plane) TMA map of a K-contiguous BF16 operand with
-// a (bk, box_rows, planes) box and the swizzle the UMMA descriptor expects.
+// Encode the 3-D TMA map of a BF16 operand with the box and swizzle the
+// UMMA descriptor expects: K-major (k, row, plane) with a (bk, box_rows,
+// planes) box; MN-major (row, k, plane) with a (64, bk, planes) box, loaded
+// box_rows / 64 times per stage.
 bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows);
 
 // Grouped launch: `count` problems described by dev_problems (device) with

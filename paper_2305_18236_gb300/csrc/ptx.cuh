@@ -357,11 +357,29 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9 = 1, bits 10-12 = 1), both operands K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc_bf16_f32(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) |
-           (uint32_t(m >> 4) << 24);
+// (bits 7-9 = 1, bits 10-12 = 1), operand majorness in bits 15 (A) and 16
+// (B): 0 = K-major, 1 = MN-major; N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc_bf16_f32(int m, int n, int a_mn = 0,
+                                                           int b_mn = 0) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a_mn & 1) << 15) |
+           (uint32_t(b_mn & 1) << 16) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor without its start address: leading byte
+// offset >> 4 in bits 16-29, stride byte offset >> 4 in bits 32-45, version
+// 1 in bits 46-47, swizzle layout in bits 61-63 (2 = 128B, 4 = 64B).
+// K-major swizzled tiles: LBO unused (16), SBO = distance between 8-row
+// groups.  MN-major 128B-swizzled tiles (64 MN elements per 128-byte row,
+// one row per K index): LBO = distance between 64-element MN groups, SBO =
+// distance between groups of 8 K rows.
+__host__ __device__ constexpr uint64_t sdesc_fields(uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    return (uint64_t((lbo >> 4) & 0x3FFF) << 16) | (uint64_t((sbo >> 4) & 0x3FFF) << 32) |
+           (1ull << 46) | (uint64_t(layout & 7) << 61);
+}
+
+// The descriptor of the tile at `smem_addr` (start address >> 4 in bits 0-13).
+__device__ __forceinline__ uint64_t sdesc_at(uint32_t smem_addr, uint64_t fields) {
+    return fields | uint64_t((smem_addr & 0x3FFFF) >> 4);
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA

@@ -4,7 +4,9 @@
 // This is the GPU form of Algorithm 1 (Kuzma et al., Section 3):
 //  * the paper's pack() calls (Algorithm 1, packing of A and B blocks into
 //    tile order, Section 3.1) become TMA tensor loads that drop swizzled
-//    BM x BK and BN x BK tiles into a multi-stage shared-memory ring;
+//    BM x BK and BN x BK tiles into a multi-stage shared-memory ring, either
+//    K-major (operand rows K-contiguous) or MN-major (an operand stored
+//    K x rows, read as 64-wide row groups without a transposing pass);
 //  * the j/i block loops become a persistent tile scheduler: each CTA walks
 //    output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... in an order
 //    that keeps `raster_group` M tiles per B panel together (the paper's
@@ -20,8 +22,9 @@
 // and lo planes of both operands and each 16-deep K slice issues
 // acc += Alo*Bhi; acc += Ahi*Blo; acc += Ahi*Bhi (small terms first).
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
-// MMA issuer, warps 2-5 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// Warp roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
+// MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31
+// and one half of the tile's columns).
 // Two accumulators (2 x BN TMEM columns) let the epilogue of tile i overlap
 // the MMAs of tile i+1.  Every wait is bounded (ptx.cuh); on expiry the
 // kernel records the error, drains its own copies and MMAs, frees TMEM and
@@ -66,6 +69,7 @@ struct TcParams {
     const int* tile_prob;  // problem index of every tile
     int count;
     int c_tma;  // epilogue writes through the C tensor map (beta == 0 or split-K partials)
+    int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
 };
 
 template <int BN, int BK, int NTERMS>
@@ -76,6 +80,9 @@ struct Shape {
     static constexpr int STAGE = PLANES * (A_PLANE + B_PLANE);
     static constexpr int TMEM_COLS = 2 * BN;  // two FP32 accumulators
     static constexpr int ROW_BYTES = BK * 2;  // 64 (SW64) or 128 (SW128)
+    // MN-major operands: 64-element MN groups of all planes (each plane BK
+    // rows of 128 bytes), one TMA box each, MN_GROUP bytes apart
+    static constexpr int MN_GROUP = PLANES * BK * 128;
     static constexpr int BAR_BYTES = 1024;    // barriers + TMEM slot + abort flag
     static constexpr int STAGING = kEpiWarps * 32 * 33 * 4;  // epilogue store slabs
     static_assert(ROW_BYTES == 64 || ROW_BYTES == 128, "BK must be 32 or 64");
@@ -92,6 +99,7 @@ struct Shape {
 struct TileInfo {
     int mt, nt, ks, kb0, kb1;
     int prob;  // problem index (grouped launches)
+    int maj;   // bit 0: A MN-major, bit 1: B MN-major
     const CUtensorMap* ma;
     const CUtensorMap* mb;
 };
@@ -127,6 +135,7 @@ __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUt
         ti.kb0 = ti.ks * p.kb_per_split;
         ti.kb1 = min(ti.kb0 + p.kb_per_split, p.k_blocks);
         ti.prob = 0;
+        ti.maj = p.maj;
         ti.ma = tmA;
         ti.mb = tmB;
     } else {
@@ -138,6 +147,7 @@ __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUt
         ti.kb0 = 0;
         ti.kb1 = __ldg(&q->k_blocks);
         ti.prob = lo;
+        ti.maj = __ldg(&q->major);
         ti.ma = p.maps + 2 * lo;
         ti.mb = p.maps + 2 * lo + 1;
     }
@@ -262,6 +272,46 @@ __device__ __forceinline__ void store_piece_tma(const float* v, float* slab, int
 // accumulator; short chunks bound that growth and the register sums carry
 // the rest of K with ordinary FP32 rounding.  Without PROMOTE a tile is one
 // chunk.
+// Where one operand's hi/lo planes and 16-deep K slices sit inside a stage,
+// and the descriptor fields that describe its tiles.  K-major: planes of
+// `rows` rows x BK (one swizzled row per operand row); a K slice is 32 bytes
+// along the rows.  MN-major: 64-element MN groups of [plane][BK rows of
+// 128 bytes]; a K slice is 16 rows = 2048 bytes down the group.
+struct OpLayout {
+    uint64_t fields;
+    uint32_t lo_off;  // hi plane -> lo plane
+    uint32_t k_step;  // one 16-deep K slice
+};
+
+template <class S>
+__device__ __forceinline__ OpLayout op_layout(int mn, int plane_bytes) {
+    OpLayout l;
+    if (mn) {
+        l.fields = sdesc_fields(S::MN_GROUP, 1024, 2);
+        l.lo_off = S::MN_GROUP / S::PLANES;
+        l.k_step = 2048;
+    } else {
+        l.fields = sdesc_fields(16, 8 * S::ROW_BYTES, S::ROW_BYTES == 128 ? 2 : 4);
+        l.lo_off = plane_bytes;
+        l.k_step = 32;
+    }
+    return l;
+}
+
+// TMA copies of one operand's BK-deep slice into a stage: one box for a
+// K-major operand, rows / 64 boxes for an MN-major one.  x coordinates are
+// multiples of BK or of 64 elements (16-byte aligned) and never negative.
+__device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* map, uint64_t* bar,
+                                             int mn, int rows, int group_bytes, int kcoord,
+                                             int row0, uint64_t pol) {
+    if (!mn) {
+        tma_load_3d(dst, map, bar, kcoord, row0, 0, pol);
+    } else {
+        for (int g = 0; g < rows / 64; ++g)
+            tma_load_3d(dst + g * group_bytes, map, bar, row0 + g * 64, kcoord, 0, pol);
+    }
+}
+
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -329,9 +379,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     uint8_t* st = smem + s * S::STAGE;
                     mbar_arrive_expect_tx(&full[s], S::STAGE);
-                    tma_load_3d(st, ti.ma, &full[s], kb * BK, ti.mt * kBM, 0, pol);
-                    tma_load_3d(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], kb * BK, ti.nt * BN,
-                                0, pol);
+                    load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kb * BK,
+                                 ti.mt * kBM, pol);
+                    load_operand(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], (ti.maj >> 1) & 1,
+                                 BN, S::MN_GROUP, kb * BK, ti.nt * BN, pol);
                     filled |= 1u << s;
                     fill_par = (fill_par & ~(1u << s)) | (ph << s);
                 }
@@ -343,12 +394,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc_bf16_f32(kBM, BN);
             int it = 0, g = 0;  // g: accumulation chunks started by this CTA
             bool ok = true;
             for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
+                const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
+                const uint32_t idesc = make_idesc_bf16_f32(kBM, BN, a_mn, b_mn);
+                const OpLayout la = op_layout<S>(a_mn, S::A_PLANE);
+                const OpLayout lb = op_layout<S>(b_mn, S::B_PLANE);
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                     const int buf = g & 1;
@@ -368,24 +422,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
-                        const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
+                        const uint32_t a_st = smem_u32(smem + s * S::STAGE);
+                        const uint32_t b_st = a_st + S::PLANES * S::A_PLANE;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t off = kk * 32;  // 16 BF16 = 32 bytes along the row
+                            const uint32_t a_hi = a_st + kk * la.k_step;
+                            const uint32_t b_hi = b_st + kk * lb.k_step;
                             const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
                             if (NTERMS == 3) {
-                                const uint32_t a_lo = a_hi + S::A_PLANE;
-                                const uint32_t b_lo = b_hi + S::B_PLANE;
-                                umma_bf16(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
-                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, acc);
-                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                          make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc, 1u);
-                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, 1u);
+                                umma_bf16(d_tmem, sdesc_at(a_hi + la.lo_off, la.fields),
+                                          sdesc_at(b_hi, lb.fields), idesc, acc);
+                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
+                                          sdesc_at(b_hi + lb.lo_off, lb.fields), idesc, 1u);
+                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
+                                          sdesc_at(b_hi, lb.fields), idesc, 1u);
                             } else {
-                                umma_bf16(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                          make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc, acc);
+                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
+                                          sdesc_at(b_hi, lb.fields), idesc, acc);
                             }
                         }
                         umma_commit(&empty[s]);  // slot free once these MMAs have read it
@@ -959,14 +1012,20 @@ void fill_common(TcParams& p, const TcLaunch& cfg, int bk, int nterms, int* err_
 bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[3] = {cuuint64_t(op.k), cuuint64_t(op.rows), cuuint64_t(op.planes)};
+    if (op.mn_major && box_rows % 64 != 0) return false;
+    // stored rows: operand rows (K-major) or K indices (MN-major)
+    const int64_t stored_rows = op.mn_major ? op.k : op.rows;
+    cuuint64_t dims[3] = {cuuint64_t(op.mn_major ? op.rows : op.k), cuuint64_t(stored_rows),
+                          cuuint64_t(op.planes)};
     cuuint64_t strides[2] = {cuuint64_t(op.ld) * 2,
-                             cuuint64_t(op.planes > 1 ? op.plane_ld : op.ld * op.rows) * 2};
-    cuuint32_t box[3] = {cuuint32_t(bk), cuuint32_t(box_rows), cuuint32_t(op.planes)};
+                             cuuint64_t(op.planes > 1 ? op.plane_ld : op.ld * stored_rows) * 2};
+    cuuint32_t box[3] = {cuuint32_t(op.mn_major ? 64 : bk), cuuint32_t(op.mn_major ? bk : box_rows),
+                         cuuint32_t(op.planes)};
     cuuint32_t estr[3] = {1, 1, 1};
+    const bool sw128 = op.mn_major || bk * 2 == 128;
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(op.base), dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    bk * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -986,8 +1045,10 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     const int bn = cfg.bn == 128 ? 128 : 256;
     const int bk = cfg.bk == 64 ? 64 : 32;
     const bool pair = cfg.cta_group == 2 && bn == 256;
+    if (pair && (a.mn_major || b.mn_major)) return -6;  // CTA pairs stage K-major tiles only
     const int bm = pair ? 2 * kBM : kBM;  // output rows per tile (per CTA pair)
     TcParams p{};
+    p.maj = (a.mn_major ? 1 : 0) | (b.mn_major ? 2 : 0);
     p.M = int(M);
     p.N = int(N);
     p.K = int(K);

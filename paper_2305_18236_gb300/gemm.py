@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import MODES, OP_N, OP_T, check, gemm_config_t, gemm_problem_t
+from ._lib import LAYOUTS, MODES, OP_N, OP_T, check, gemm_config_t, gemm_problem_t
 
 __all__ = ["Gemm", "handle", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
            "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "sync"]
@@ -66,9 +66,12 @@ class Gemm:
 
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
-                   promote_k=0, cta_group=0, wait_poll_limit=0):
+                   promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="as_stored"):
+        """operand_layout: "as_stored" (MN-major tiles for operands stored
+        K x rows) or "k_major" (every operand made K-contiguous first)."""
+        layout = LAYOUTS[operand_layout] if isinstance(operand_layout, str) else operand_layout
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
-                            wait_poll_limit)
+                            wait_poll_limit, layout, 0)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
 
     def reset_config(self):
@@ -267,7 +270,8 @@ class GroupedPlan:
         check(self.lib.gemm_grouped_plan_config(self.plan, ctypes.byref(cfg), ctypes.byref(ms)),
               "gemm_grouped_plan_config")
         return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
-                "raster_group": cfg.raster_group, "tuned_ms": ms.value}
+                "raster_group": cfg.raster_group, "operand_layout": cfg.operand_layout,
+                "tuned_ms": ms.value}
 
     def close(self):
         if self.plan:
