@@ -13,6 +13,8 @@ loop nest computes alpha * op(A) op(B) + beta * C with beta applied once):
   their BF16 split parts (not in the paper; the definition is stated in
   ``gemm_ref.c``).
 * ``split_bf16`` / ``bf16_bits_to_f32`` -- the hi/lo BF16 split.
+* ``syr2k`` -- one triangle of C = alpha (opA opB^T + opB opA^T) + beta C,
+  the rank-2k update of Section 6.1 (exact or with split products).
 * ``normwise_error`` -- max |C - C64| / max D, the error measure.
 
 Every function is pinned by ``tests/test_oracle_pins.py``; none is unpinned.
@@ -41,6 +43,10 @@ def _declare(lib):
                                             ctypes.c_double, f32p, i64, f32p, i64,
                                             ctypes.c_double, f32p, i64, ctypes.c_int,
                                             i64p, i64, f64p, ctypes.c_int]
+    lib.oracle_syr2k.restype = ctypes.c_int
+    lib.oracle_syr2k.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, ctypes.c_double,
+                                 f32p, i64, f32p, i64, ctypes.c_double, f32p, i64,
+                                 ctypes.c_int, i64p, i64, f64p, f64p, ctypes.c_int]
     lib.oracle_split.restype = None
     lib.oracle_split.argtypes = [f32p, i64, u16p, u16p]
     lib.oracle_bf16_rne.restype = ctypes.c_uint16
@@ -64,7 +70,7 @@ def load_variant(path):
         pass
 
     b = _Bound()
-    for name in ("gemm", "gemm_split_terms", "split_bf16"):
+    for name in ("gemm", "gemm_split_terms", "split_bf16", "syr2k"):
         fn = globals()[name]
         setattr(b, name, (lambda f: lambda *a, **k: f(*a, _library=lib, **k))(fn))
     b.normwise_error = normwise_error
@@ -166,6 +172,52 @@ def gemm_split_terms(A, B, terms, alpha=1.0, beta=0.0, C0=None, transA=False,
                               C64.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                               int(threads))
     return C64
+
+
+def syr2k(A, B, alpha=1.0, beta=0.0, C0=None, uplo="lower", trans=False, terms=0, rows=None,
+          threads=0, want_denominator=True, _library=None):
+    """One triangle of alpha (opA opB^T + opB opA^T) + beta C0 in FP64.
+
+    opX = X (stored N x K) or X.T (X stored K x N, ``trans``).  Entries outside
+    the ``uplo`` triangle ("lower": j <= i, "upper": j >= i) hold C0 (0 when
+    C0 is None) and a zero denominator.  ``terms`` != 0 replaces every product
+    by the selected BF16 split cross products (bits as in gemm_split_terms).
+    Returns (C64, D, threads_used) for the requested rows.
+    """
+    l = _library or _load()
+    A = np.asarray(A)
+    B = np.asarray(B)
+    if A.shape != B.shape:
+        raise ValueError("A and B must have the same shape")
+    N, K = (A.shape[1], A.shape[0]) if trans else A.shape
+    if uplo not in ("lower", "upper"):
+        raise ValueError("uplo is 'lower' or 'upper'")
+    pa, lda, ka = _f32_view(A)
+    pb, ldb, kb = _f32_view(B)
+    if C0 is not None:
+        if C0.shape != (N, N):
+            raise ValueError("C0 shape")
+        pc, ldc, kc = _f32_view(C0)
+    elif beta != 0.0:
+        raise ValueError("beta != 0 needs C0")
+    else:
+        pc, ldc, kc = None, max(1, N), None
+    if rows is None:
+        nrows, prow, krow = N, None, None
+    else:
+        krow = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        if krow.size and (krow.min() < 0 or krow.max() >= N):
+            raise ValueError("row index out of range")
+        nrows = krow.size
+        prow = krow.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    C64 = np.zeros((nrows, N), dtype=np.float64)
+    D = np.zeros((nrows, N), dtype=np.float64) if want_denominator else None
+    used = l.oracle_syr2k(0 if uplo == "lower" else 1, int(bool(trans)), N, K, float(alpha),
+                          pa, lda, pb, ldb, float(beta), pc, ldc, int(terms), prow, nrows,
+                          C64.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          D.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if D is not None else None,
+                          int(threads))
+    return C64, D, used
 
 
 def split_bf16(x, _library=None):

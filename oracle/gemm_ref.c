@@ -31,6 +31,9 @@
  * rounding the dropped 16 bits to nearest with ties to even; for
  * non-finite hi, lo = 0.
  *
+ * The file also holds the SYR2K update of Section 6.1 (oracle_syr2k, at
+ * the end), written out from its definition in the same way.
+ *
  * Parity of every function here is pinned by the CPU tests against brute
  * force in exact rational arithmetic, closed forms and library routines.
  */
@@ -231,5 +234,106 @@ int oracle_gemm_split_terms(int transA, int transB, int64_t M, int64_t N, int64_
     }
     free(bh);
     free(bl);
+    return used;
+}
+
+/*
+ * SYR2K, the rank-2k update used as the example of Section 6.1 (macro-level
+ * strategy for other BLAS kernels): one triangle of the symmetric C,
+ *
+ *   C64[i][j] = alpha * sum_p ( opA[i][p] opB[j][p] + opB[i][p] opA[j][p] )
+ *             + beta * C0[i][j]
+ *
+ * for (i, j) in the triangle -- uplo 0: j <= i (lower), uplo 1: j >= i
+ * (upper), diagonal included -- where opX is X (stored N x K, trans == 0)
+ * or X^T (X stored K x N, trans == 1).  That is C <- alpha (A B^T + B A^T)
+ * + beta C, or alpha (A^T B + B^T A) + beta C, the two GEMM updates of each
+ * block that Section 6.1 describes.  Both products of one p are summed
+ * first and then accumulated in increasing p, so C64[i][j] of the lower
+ * triangle equals C64[j][i] of the upper one bit for bit.
+ *
+ * Entries outside the triangle are not part of the update: C64 holds C0
+ * there (0 when C0 is NULL) and D holds 0.  Same readings as oracle_gemm:
+ * beta == 0 does not read C0 inside the triangle, alpha == 0 does not read
+ * A or B.
+ *
+ * terms == 0: exact FP64 products; otherwise every product x*y is replaced
+ * by the selected cross products of the BF16 split parts of x and y, with
+ * the bits of oracle_gemm_split_terms (x plays the A role: opA[i] in the
+ * first product, opB[i] in the second).  D is the error denominator
+ * |alpha| sum_p (|opA[i][p] opB[j][p]| + |opB[i][p] opA[j][p]|) + |beta||C0|
+ * from the unsplit values.  rows/nrows as in oracle_gemm; C64 and D are
+ * nrows x N.
+ */
+static double split_product(float x, float y, int terms)
+{
+    uint16_t xh, xl, yh, yl;
+    oracle_split(&x, 1, &xh, &xl);
+    oracle_split(&y, 1, &yh, &yl);
+    double ah = (double)oracle_bf16_to_float(xh), al = (double)oracle_bf16_to_float(xl);
+    double bh = (double)oracle_bf16_to_float(yh), bl = (double)oracle_bf16_to_float(yl);
+    double s = 0.0;
+    if (terms & 1) s += ah * bh;
+    if (terms & 2) s += ah * bl;
+    if (terms & 4) s += al * bh;
+    if (terms & 8) s += al * bl;
+    return s;
+}
+
+int oracle_syr2k(int uplo, int trans, int64_t N, int64_t K, double alpha,
+                 const float *A, int64_t lda, const float *B, int64_t ldb,
+                 double beta, const float *C0, int64_t ldc0, int terms,
+                 const int64_t *rows, int64_t nrows, double *C64, double *D,
+                 int nthreads)
+{
+    int used = 1;
+    if (rows == NULL)
+        nrows = N;
+#ifdef _OPENMP
+    if (nthreads <= 0)
+        nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#else
+    (void)nthreads;
+#endif
+    for (int64_t r = 0; r < nrows; ++r) {
+#ifdef _OPENMP
+        if (r == 0)
+            used = omp_get_num_threads();
+#endif
+        int64_t i = rows ? rows[r] : r;
+        for (int64_t j = 0; j < N; ++j) {
+            int inside = uplo == 0 ? (j <= i) : (j >= i);
+            if (!inside) {
+                C64[r * N + j] = C0 ? (double)C0[i * ldc0 + j] : 0.0;
+                if (D)
+                    D[r * N + j] = 0.0;
+                continue;
+            }
+            double acc = 0.0, mag = 0.0;
+            if (alpha != 0.0) {
+                for (int64_t p = 0; p < K; ++p) {
+                    double aip = op_at(A, lda, trans, i, p), bjp = op_at(B, ldb, trans, j, p);
+                    double bip = op_at(B, ldb, trans, i, p), ajp = op_at(A, lda, trans, j, p);
+                    if (terms == 0)
+                        acc += aip * bjp + bip * ajp;
+                    else
+                        acc += split_product((float)aip, (float)bjp, terms) +
+                               split_product((float)bip, (float)ajp, terms);
+                    mag += fabs(aip) * fabs(bjp) + fabs(bip) * fabs(ajp);
+                }
+            }
+            double c = alpha * acc;
+            double d = fabs(alpha) * mag;
+            if (beta != 0.0) {
+                double c0 = (double)C0[i * ldc0 + j];
+                c += beta * c0;
+                d += fabs(beta) * fabs(c0);
+            }
+            C64[r * N + j] = c;
+            if (D)
+                D[r * N + j] = d;
+        }
+    }
     return used;
 }

@@ -292,8 +292,178 @@ def check_split_terms_reduce(orc):
     assert np.array_equal(orc.gemm_split_terms(iA, iB, 15), plain)
 
 
+# ------------------------------------------------------------------ SYR2K
+# Section 6.1: one triangle of C <- alpha (opA opB^T + opB opA^T) + beta C,
+# opX = X (stored N x K) or X^T (stored K x N); the other triangle is not
+# part of the update.
+
+UPLOS = ["lower", "upper"]
+
+
+def _inside(i, j, uplo):
+    return j <= i if uplo == "lower" else j >= i
+
+
+def _syr2k_exact(opA, opB, alpha, beta, C0, uplo, parts=None):
+    """Exact rational triangle (dict (i, j) -> (C, D)); with ``parts`` the
+    products are sums over (x-part of row i, y-part of row j) pairs."""
+    N, K = opA.shape
+    fa, fb = Fraction(float(alpha)), Fraction(float(beta))
+    out = {}
+    for i, j in product(range(N), range(N)):
+        if not _inside(i, j, uplo):
+            continue
+        s = Fraction(0)
+        m = Fraction(0)
+        for x, y in ((opA, opB), (opB, opA)):
+            for p in range(K):
+                xv, yv = Fraction(float(x[i, p])), Fraction(float(y[j, p]))
+                m += abs(xv) * abs(yv)
+                if parts is None:
+                    s += xv * yv
+                else:
+                    for px, py in parts(x is opA):
+                        s += Fraction(float(px[i, p])) * Fraction(float(py[j, p]))
+        c = fa * s
+        d = abs(fa) * m
+        if beta != 0.0:
+            c0 = Fraction(float(C0[i, j]))
+            c += fb * c0
+            d += abs(fb) * abs(c0)
+        out[i, j] = (c, d)
+    return out
+
+
+def _check_outside(C64, D, C0, uplo):
+    N = C64.shape[0]
+    for i, j in product(range(N), range(N)):
+        if not _inside(i, j, uplo):
+            assert C64[i, j] == C0[i, j] and D[i, j] == 0.0, ("outside", i, j)
+
+
+def check_syr2k_brute_force(orc):
+    """Exact rational sums on tiny shapes, both triangles, both trans, several
+    alpha/beta; entries outside the triangle are C0 with zero denominator."""
+    for (N, K), uplo, trans, (alpha, beta) in product(
+            [(1, 1), (4, 3), (6, 5), (9, 2)], UPLOS, [False, True],
+            [(1.0, 0.0), (1.5, 0.5), (-0.75, 2.0)]):
+        opA = inputs.uniform((N, K), 61)
+        opB = inputs.log_uniform((N, K), 62, -3.0, 3.0)
+        C0 = inputs.uniform((N, N), 63)
+        C64, D, _ = orc.syr2k(_stored(opA, trans), _stored(opB, trans), alpha, beta, C0,
+                              uplo=uplo, trans=trans)
+        u = 2.0 ** -53
+        for (i, j), (c, d) in _syr2k_exact(opA, opB, alpha, beta, C0, uplo).items():
+            bound = Fraction(2.0 * (2 * K + 3) * u * float(d))
+            assert abs(Fraction(float(C64[i, j])) - c) <= bound, ("C", N, K, uplo, trans, i, j)
+            assert abs(Fraction(float(D[i, j])) - d) <= bound, ("D", N, K, uplo, trans, i, j)
+        _check_outside(C64, D, C0, uplo)
+
+
+def check_syr2k_vs_library(orc):
+    """The triangle of numpy's FP64 alpha (A B^T + B A^T) + beta C0."""
+    N, K = 37, 23
+    opA = inputs.uniform((N, K), 64)
+    opB = inputs.uniform((N, K), 65)
+    C0 = inputs.uniform((N, N), 66)
+    a, b = opA.astype(np.float64), opB.astype(np.float64)
+    ref = 1.5 * (a @ b.T + b @ a.T) + 0.5 * C0.astype(np.float64)
+    den = 1.5 * (np.abs(a) @ np.abs(b).T + np.abs(b) @ np.abs(a).T) + 0.5 * np.abs(C0)
+    for uplo, trans in product(UPLOS, [False, True]):
+        C64, D, _ = orc.syr2k(_stored(opA, trans), _stored(opB, trans), 1.5, 0.5, C0,
+                              uplo=uplo, trans=trans)
+        mask = np.tril(np.ones((N, N), bool)) if uplo == "lower" else np.triu(np.ones((N, N), bool))
+        assert np.max(np.abs(C64 - ref)[mask] / den[mask]) <= 1e-14
+        assert np.max(np.abs(D - den)[mask] / den[mask]) <= 1e-14
+        _check_outside(C64, D, C0, uplo)
+
+
+def check_syr2k_integers(orc):
+    """Integer data (every FP64 sum exact): A B^T + B A^T against numpy int64,
+    and B = A giving the rank-k closed form 2 A A^T."""
+    N, K = 20, 30
+    iA = inputs.integers((N, K), 67)
+    iB = inputs.integers((N, K), 68)
+    C0 = inputs.integers((N, N), 69)
+    a, b, c0 = iA.astype(np.int64), iB.astype(np.int64), C0.astype(np.int64)
+    for uplo, trans in product(UPLOS, [False, True]):
+        mask = np.tril(np.ones((N, N), bool)) if uplo == "lower" else np.triu(np.ones((N, N), bool))
+        C64, _, _ = orc.syr2k(_stored(iA, trans), _stored(iB, trans), 1.0, 1.0, C0, uplo=uplo,
+                              trans=trans)
+        assert np.array_equal(C64[mask], (a @ b.T + b @ a.T + c0)[mask].astype(np.float64))
+        C64, _, _ = orc.syr2k(_stored(iA, trans), _stored(iA, trans), 1.0, 0.0, uplo=uplo,
+                              trans=trans)
+        assert np.array_equal(C64[mask], (2 * (a @ a.T))[mask].astype(np.float64))
+
+
+def check_syr2k_symmetry(orc):
+    """With symmetric C0, the upper triangle is the transpose of the lower
+    one, bit for bit (each entry sums the same pairs in the same order)."""
+    N, K = 15, 40
+    opA = inputs.uniform((N, K), 70)
+    opB = inputs.log_uniform((N, K), 71)
+    S = inputs.uniform((N, N), 72)
+    C0 = np.ascontiguousarray(np.tril(S) + np.tril(S, -1).T)
+    for trans in (False, True):
+        lo, _, _ = orc.syr2k(_stored(opA, trans), _stored(opB, trans), 1.5, 0.5, C0,
+                             uplo="lower", trans=trans)
+        up, _, _ = orc.syr2k(_stored(opA, trans), _stored(opB, trans), 1.5, 0.5, C0,
+                             uplo="upper", trans=trans)
+        assert np.array_equal(np.tril(lo), np.tril(up.T))
+
+
+def check_syr2k_special(orc):
+    """beta == 0 never reads C0 inside the triangle (NaN there stays out);
+    alpha == 0 and K == 0 give beta C0 exactly; row subsets are rows."""
+    N, K = 11, 7
+    opA = inputs.uniform((N, K), 73)
+    opB = inputs.uniform((N, K), 74)
+    C0 = inputs.uniform((N, N), 75)
+    nanC = C0.copy()
+    nanC[np.tril_indices(N)] = np.nan
+    C64, _, _ = orc.syr2k(opA, opB, 1.0, 0.0, nanC, uplo="lower")
+    assert np.all(np.isfinite(np.tril(C64)))
+    assert np.array_equal(np.triu(C64, 1), np.triu(C0, 1).astype(np.float64))
+    nanA = np.full((N, K), np.nan, np.float32)
+    for uplo in UPLOS:
+        mask = np.tril(np.ones((N, N), bool)) if uplo == "lower" else np.triu(np.ones((N, N), bool))
+        C64, _, _ = orc.syr2k(nanA, nanA, 0.0, 0.5, C0, uplo=uplo)
+        assert np.array_equal(C64[mask], (0.5 * C0.astype(np.float64))[mask])
+        C64, _, _ = orc.syr2k(np.zeros((N, 0), np.float32), np.zeros((N, 0), np.float32), 1.0,
+                              0.25, C0, uplo=uplo)
+        assert np.array_equal(C64[mask], (0.25 * C0.astype(np.float64))[mask])
+        full, Df, _ = orc.syr2k(opA, opB, 1.5, 0.5, C0, uplo=uplo)
+        rows = np.array([10, 0, 4, 4])
+        sub, Ds, _ = orc.syr2k(opA, opB, 1.5, 0.5, C0, uplo=uplo, rows=rows)
+        assert np.array_equal(sub, full[rows]) and np.array_equal(Ds, Df[rows])
+
+
+def check_syr2k_split_terms(orc):
+    """Split products: each selection of cross products against exact rational
+    sums of torch-split operands (x in the A role: opA in the first product,
+    opB in the second)."""
+    N, K = 5, 4
+    opA = inputs.uniform((N, K), 76)
+    opB = inputs.log_uniform((N, K), 77, -4.0, 4.0)
+    C0 = inputs.uniform((N, N), 78)
+    ah, al = _torch_split(opA)
+    bh, bl = _torch_split(opB)
+    for terms, uplo, trans in product([1, 2, 4, 7, 15], UPLOS, [False, True]):
+        def parts(first, terms=terms):
+            xh, xl, yh, yl = (ah, al, bh, bl) if first else (bh, bl, ah, al)
+            sel = {1: (xh, yh), 2: (xh, yl), 4: (xl, yh), 8: (xl, yl)}
+            return [v for bit, v in sel.items() if terms & bit]
+        C64, _, _ = orc.syr2k(_stored(opA, trans), _stored(opB, trans), 1.5, 0.5, C0,
+                              uplo=uplo, trans=trans, terms=terms)
+        for (i, j), (c, d) in _syr2k_exact(opA, opB, 1.5, 0.5, C0, uplo, parts).items():
+            bound = Fraction(2.0 * (8 * K + 3) * 2.0 ** -53) * d
+            assert abs(Fraction(float(C64[i, j])) - c) <= bound, (terms, uplo, trans, i, j)
+
+
 ALL_CHECKS = [check_brute_force, check_identity, check_permutation, check_all_ones,
               check_integers, check_transpose_identity, check_blocked_k,
               check_alpha_beta_special, check_rows_subset, check_denominator,
               check_split_vs_library, check_split_invariants,
-              check_split_terms_brute_force, check_split_terms_reduce]
+              check_split_terms_brute_force, check_split_terms_reduce,
+              check_syr2k_brute_force, check_syr2k_vs_library, check_syr2k_integers,
+              check_syr2k_symmetry, check_syr2k_special, check_syr2k_split_terms]

@@ -53,6 +53,19 @@ MUTANTS = {
     "rows_ignored": ("int64_t i = rows ? rows[r] : r;\n            for (int64_t j = 0; j < N; ++j) {\n                acc[j] = 0.0;\n                mag[j] = 0.0;",
                      "int64_t i = r;\n            for (int64_t j = 0; j < N; ++j) {\n                acc[j] = 0.0;\n                mag[j] = 0.0;"),
     "beta_read_when_zero": ("if (beta != 0.0) {\n                    double c0", "if (1) {\n                    double c0"),
+    # SYR2K (Section 6.1)
+    "syr2k_second_product_dropped": ("acc += aip * bjp + bip * ajp;", "acc += aip * bjp;"),
+    "syr2k_wrong_operand": ("acc += aip * bjp + bip * ajp;", "acc += aip * bjp + aip * ajp;"),
+    "syr2k_diagonal_excluded": ("int inside = uplo == 0 ? (j <= i) : (j >= i);",
+                                "int inside = uplo == 0 ? (j < i) : (j >= i);"),
+    "syr2k_triangle_swapped": ("int inside = uplo == 0 ? (j <= i) : (j >= i);",
+                               "int inside = uplo == 0 ? (j >= i) : (j <= i);"),
+    "syr2k_outside_scaled": ("C64[r * N + j] = C0 ? (double)C0[i * ldc0 + j] : 0.0;",
+                             "C64[r * N + j] = C0 ? beta * (double)C0[i * ldc0 + j] : 0.0;"),
+    "syr2k_split_roles": ("split_product((float)bip, (float)ajp, terms);",
+                          "split_product((float)ajp, (float)bip, terms);"),
+    "syr2k_denominator_signed": ("mag += fabs(aip) * fabs(bjp) + fabs(bip) * fabs(ajp);",
+                                 "mag += aip * bjp + bip * ajp;"),
 }
 
 
