@@ -50,9 +50,11 @@ def parse():
     p.add_argument("--operand-layout", default="as_stored", choices=["as_stored", "k_major"],
                    help="as_stored: operands stored K x rows are split without transposing and "
                         "read as MN-major tiles; k_major: every operand made K-contiguous first")
-    p.add_argument("--workload", default="square", choices=["square", "rect", "grouped", "chain"],
+    p.add_argument("--workload", default="square",
+                   choices=["square", "rect", "grouped", "chain", "syr2k"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
-                        "grouped: 512 uneven problems; chain: Y = X W forward + backward")
+                        "grouped: 512 uneven problems; chain: Y = X W forward + backward; "
+                        "syr2k: the rank-2k update of Section 6.1 at N = K = --size")
     return p.parse_args()
 
 
@@ -587,6 +589,89 @@ def run_chain(args):
           flush=True)
 
 
+def run_syr2k(args):
+    """SYR2K (Section 6.1): lower triangle of C <- 1.5 (A B^T + B A^T) + 0.5 C,
+    A, B FP32 N x K U[-1, 1], N = K = --size; the chosen mode against the
+    FP32 SIMT variant, sampled rows against the FP64 oracle."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+
+    torch.cuda.set_device(0)
+    n = args.size
+    gen = torch.Generator(device="cuda").manual_seed(SEED)
+    A = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    B = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    C0 = torch.rand((n, n), device="cuda", generator=gen) * 2 - 1
+    C = C0.clone()
+    h = g.Gemm()
+    h.set_config(operand_layout=args.operand_layout)
+    stream = torch.cuda.current_stream()
+    peaks, src = load_peaks()
+    flops = 2.0 * n * n * n  # useful flops of one triangle: 2 N^2 K
+
+    def timed(mode, steps, warmup):
+        run = lambda: g.syr2k(A, B, C=C, alpha=ALPHA, beta=BETA, uplo="lower", mode=mode, h=h)
+        run()
+        torch.cuda.synchronize()
+        launches = h.last_launch_count()
+        h.lib.gemm_profile_enable(h.h, 1)
+        ms = _events_ms(run, steps, warmup, stream)
+        main_ms, main_n = ctypes.c_double(), ctypes.c_int()
+        h.lib.gemm_profile_read(h.h, ctypes.byref(main_ms), ctypes.byref(main_n))
+        h.lib.gemm_profile_enable(h.h, 0)
+        return ms, main_ms.value / max(1, main_n.value), launches
+
+    ms, kernel_ms, launches = timed(args.mode, args.steps, args.warmup)
+    # tensor work of the kernel: every 128 x BN tile that meets the triangle,
+    # in full, over both products (3 BF16 products each in the split mode)
+    bn = 256
+    tiles = sum(min(-(-n // bn), (128 * mt + 127) // bn + 1) for mt in range(-(-n // 128)))
+    tensor_flops = tiles * 128 * bn * 2.0 * (2 * n) * (3 if args.mode == "bf16x3" else 1)
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    line = {"metric": "SYR2K TFLOP/s (2 N^2 K) at N = K = %d" % n, "value": flops / ms / 1e9,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "dtype": args.mode, "data": "synthetic",
+            "config": {"workload": "syr2k lower, A,B %dx%d U[-1,1], alpha 1.5 beta 0.5" % (n, n),
+                       "operand_layout": args.operand_layout},
+            "launches_per_step": launches, "peaks_source": src}
+    if args.mode != "f32_simt":
+        line["roofline"] = {"bound": "tensor", "achieved": tensor_flops / kernel_ms / 1e9,
+                            "peak": peak, "unit": "TFLOP/s", "frac": tensor_flops / kernel_ms / 1e9 / peak,
+                            "kernel_ms": kernel_ms, "tiles": tiles}
+    if not args.no_compare:
+        sms, sk, _ = timed("f32_simt", max(2, args.steps // 10), 1)
+        line["compare"] = {"f32_simt_ms": sms, "f32_simt_tflops": flops / sms / 1e9,
+                           "speedup_vs_f32_simt": sms / ms}
+    if not args.no_cpu:
+        # CPU baseline: the FP64 oracle on sampled rows of the triangle; the
+        # same rows give the error of a fresh GPU call
+        C.copy_(C0)
+        g.syr2k(A, B, C=C, alpha=ALPHA, beta=BETA, uplo="lower", mode=args.mode, h=h)
+        torch.cuda.synchronize()
+        import oracle
+
+        rows = np.linspace(0, n - 1, 6).astype(np.int64)
+        hA, hB, hC0 = A.cpu().numpy(), B.cpu().numpy(), C0.cpu().numpy()
+        t0 = time.perf_counter()
+        C64, D, used = oracle.syr2k(hA, hB, ALPHA, BETA, hC0, uplo="lower", rows=rows)
+        cpu_s = time.perf_counter() - t0
+        row_flops = sum(2.0 * 2 * (int(r) + 1) * n for r in rows)
+        line["cpu_baseline"] = {"value": row_flops / cpu_s / 1e12, "unit": "TFLOP/s",
+                                "cores": used, "kind": "oracle",
+                                "sample": "%d evenly spaced rows of the lower triangle, FP64"
+                                          % len(rows)}
+        line["normwise_error"] = oracle.normwise_error(C.cpu().numpy()[rows], C64, D)
+    h.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -597,6 +682,8 @@ def main():
         run_grouped(args)
     elif args.workload == "chain":
         run_chain(args)
+    elif args.workload == "syr2k":
+        run_syr2k(args)
     else:
         run_ours(args)
 

@@ -255,6 +255,34 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t plan, gemm_config_t *
 /* Synchronise the device and free the plan.  NULL is accepted. */
 gemm_status_t gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
 
+/* Triangle selector of gemm_syr2k (diagonal included in both). */
+typedef enum { GEMM_LOWER = 0, GEMM_UPPER = 1 } gemm_uplo_t;
+
+/* SYR2K, the rank-2k update of Section 6.1 ("macro-level strategy for other
+ * BLAS kernels"): on the `uplo` triangle of the N x N matrix C,
+ *   trans == GEMM_OP_N: C <- alpha (A B^T + B A^T) + beta C, A and B N x K;
+ *   trans == GEMM_OP_T: C <- alpha (A^T B + B^T A) + beta C, A and B K x N;
+ * row-major FP32, device pointers, asynchronous on `stream`.  Elements of C
+ * outside the triangle are neither read nor written; inside it C is not read
+ * when beta == 0, and K == 0 or alpha == 0 give C <- beta C without reading A
+ * or B.  Each C block is updated by the pair of GEMM products the section
+ * describes, computed as one K loop of twice the length: the tensor-core
+ * modes split A and B once into one workspace buffer and stage A-side rows of
+ * A with B-side rows of B, then the reverse; only tiles that meet the
+ * triangle are computed.  Modes as in gemm() (GEMM_MODE_F32_SIMT runs the
+ * SIMT kernel's SYR2K variant).  Positions for GEMM_ERR_ARG: 1 handle,
+ * 2 uplo, 3 trans, 4 N, 5 K, 6 alpha, 7 A, 8 lda, 9 B, 10 ldb, 11 beta, 12 C,
+ * 13 ldc, 14 mode, 15 stream.  Workspace: gemm_syr2k_workspace_size. */
+gemm_status_t gemm_syr2k(gemm_handle_t handle, gemm_uplo_t uplo, gemm_op_t trans,
+                         int64_t N, int64_t K, float alpha,
+                         const float *A, int64_t lda, const float *B, int64_t ldb,
+                         float beta, float *C, int64_t ldc, gemm_mode_t mode, void *stream);
+
+/* Bytes of workspace gemm_syr2k needs (the split planes of A and B; 0 for
+ * GEMM_MODE_F32_SIMT or invalid arguments). */
+size_t gemm_syr2k_workspace_size(gemm_handle_t handle, gemm_mode_t mode, gemm_op_t trans,
+                                 int64_t N, int64_t K);
+
 /* Gradients of C = op(A) op(B) (alpha = 1, beta = 0) for a given dC:
  *   dA = dC op(B)^T  (stored like A: M x K, or K x M when transA == T),
  *   dB = op(A)^T dC  (stored like B).

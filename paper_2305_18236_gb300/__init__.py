@@ -13,7 +13,8 @@ built by :func:`build.build`; importing this package does not load it.
 from . import inputs  # noqa: F401  (seeded synthetic matrices; no CUDA)
 
 __all__ = ["inputs", "build_library", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
-           "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "Gemm", "handle", "sync"]
+           "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "Gemm", "handle", "sync",
+           "syr2k"]
 
 
 def build_library(force=False):
@@ -26,7 +27,7 @@ def __getattr__(name):
     # Torch-facing API is imported lazily so that `inputs` stays usable
     # without torch's CUDA initialisation.
     if name in ("matmul", "matmul_bf16", "split_bf16", "gemm_from_host", "gemm_backward",
-                "gemm_grouped", "GroupedPlan", "GemmFn", "Gemm", "handle", "sync"):
+                "gemm_grouped", "GroupedPlan", "GemmFn", "Gemm", "handle", "sync", "syr2k"):
         from . import gemm as _g
 
         return getattr(_g, name)

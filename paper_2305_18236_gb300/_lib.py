@@ -15,6 +15,8 @@ MODE_F32_SIMT, MODE_BF16, MODE_BF16X3 = 0, 1, 2
 MODES = {"f32_simt": MODE_F32_SIMT, "simt": MODE_F32_SIMT, "bf16": MODE_BF16,
          "bf16x3": MODE_BF16X3}
 
+LOWER, UPPER = 0, 1
+UPLOS = {"lower": LOWER, "upper": UPPER}
 LAYOUT_AS_STORED, LAYOUT_K_MAJOR = 0, 1
 LAYOUTS = {"as_stored": LAYOUT_AS_STORED, "k_major": LAYOUT_K_MAJOR}
 
@@ -70,6 +72,9 @@ _SIGS = {
     "gemm_backward": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _i64,
                                      _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, ctypes.c_int,
                                      _vp]),
+    "gemm_syr2k": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64, _f32, _vp, _i64,
+                                  _vp, _i64, _f32, _vp, _i64, ctypes.c_int, _vp]),
+    "gemm_syr2k_workspace_size": (_sz, [_vp, ctypes.c_int, ctypes.c_int, _i64, _i64]),
     "gemm_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "gemm_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int)]),

@@ -310,6 +310,32 @@ TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
 }
 }  // namespace gb300
 
+namespace {
+
+// SYR2K workspace: the split planes of both operands in one buffer (X then Y,
+// each P planes of the same packed layout) so that one tensor map reaches
+// both matrices by plane index.
+struct Syr2kPlan {
+    OpPlan op;
+    int planes;  // P per operand
+    size_t bytes;
+};
+
+Syr2kPlan plan_syr2k(const gemm_context* h, int nterms, int trans, int64_t N, int64_t K,
+                     TcLaunch* cfg) {
+    *cfg = plan_tc(h, nterms, N, N, K);
+    cfg->split_k = 1;
+    cfg->cta_group = 1;
+    Syr2kPlan sp;
+    sp.planes = nterms == 3 ? 2 : 1;
+    // an operand stored K x N (trans) stays MN-major unless K-major is asked for
+    sp.op = plan_op(N, K, trans == GEMM_OP_T, *cfg);
+    sp.bytes = align_up(size_t(2 * sp.planes) * size_t(sp.op.lay.plane) * 2);
+    return sp;
+}
+
+}  // namespace
+
 extern "C" {
 
 gemm_status_t gemm_create(gemm_handle_t* handle) {
@@ -659,6 +685,73 @@ gemm_status_t gemm_backward(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB,
         total += h->last_launches;
     }
     h->last_launches = total;
+    return GEMM_OK;
+}
+
+size_t gemm_syr2k_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t trans, int64_t N,
+                                 int64_t K) {
+    if (!h || N <= 0 || K <= 0) return 0;
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
+    if (trans != GEMM_OP_N && trans != GEMM_OP_T) return 0;
+    TcLaunch cfg;
+    return plan_syr2k(h, mode == GEMM_MODE_BF16X3 ? 3 : 1, trans, N, K, &cfg).bytes;
+}
+
+gemm_status_t gemm_syr2k(gemm_handle_t h, gemm_uplo_t uplo, gemm_op_t trans, int64_t N, int64_t K,
+                         float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                         float beta, float* C, int64_t ldc, gemm_mode_t mode, void* stream) {
+    if (!h) return fail_arg(h, 1);
+    h->last_err_arg = 0;
+    h->last_launches = 0;
+    if (uplo != GEMM_LOWER && uplo != GEMM_UPPER) return fail_arg(h, 2);
+    if (trans != GEMM_OP_N && trans != GEMM_OP_T) return fail_arg(h, 3);
+    if (N < 0) return fail_arg(h, 4);
+    if (K < 0) return fail_arg(h, 5);
+    const bool reads_ab = N > 0 && K > 0 && alpha != 0.0f;
+    if (reads_ab && !A) return fail_arg(h, 7);
+    if (!ld_ok(lda, trans ? N : K)) return fail_arg(h, 8);
+    if (reads_ab && !B) return fail_arg(h, 9);
+    if (!ld_ok(ldb, trans ? N : K)) return fail_arg(h, 10);
+    if (N > 0 && !C) return fail_arg(h, 12);
+    if (!ld_ok(ldc, N)) return fail_arg(h, 13);
+    if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3)
+        return fail_arg(h, 14);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int tri = uplo == GEMM_LOWER ? 1 : 2;
+    if (N == 0) return GEMM_OK;
+    if (!reads_ab) {  // C <- beta C on the triangle
+        h->last_launches = 1;
+        return status_of(gb300::launch_scale_c(N, N, beta, C, ldc, s, tri));
+    }
+    if (too_large(N, N, 2 * K)) return GEMM_ERR_UNSUPPORTED;
+    if (mode == GEMM_MODE_F32_SIMT) {
+        h->last_launches = 1;
+        ProfScope prof(h, s);
+        return status_of(gb300::launch_simt_syr2k(tri, trans, N, K, alpha, A, lda, B, ldb, beta, C,
+                                                  ldc, s));
+    }
+    const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
+    TcLaunch cfg;
+    const Syr2kPlan sp = plan_syr2k(h, nterms, trans, N, K, &cfg);
+    uint8_t* ws;
+    gemm_status_t st = get_ws(h, sp.bytes, &ws);
+    if (st != GEMM_OK) return st;
+    uint16_t* x_hi = reinterpret_cast<uint16_t*>(ws);
+    uint16_t* y_hi = x_hi + size_t(sp.planes) * size_t(sp.op.lay.plane);
+    if (split_op(sp.op, N, K, A, lda, x_hi, sp.planes, s) != cudaSuccess ||
+        split_op(sp.op, N, K, B, ldb, y_hi, sp.planes, s) != cudaSuccess)
+        return GEMM_ERR_CUDA;
+    TcOperand xy = operand_of(sp.op, x_hi, N, K, 2 * sp.planes);
+    xy.box_planes = sp.planes;
+    int launches = 2;
+    int rc;
+    {
+        ProfScope prof(h, s);
+        rc = gb300::launch_tc_syr2k(xy, nterms, tri, N, K, alpha, beta, C, ldc, cfg, h->err_word,
+                                    h->num_sms, s, &launches);
+    }
+    if (rc != 0) return static_cast<gemm_status_t>(rc);
+    h->last_launches = launches;
     return GEMM_OK;
 }
 

@@ -36,6 +36,7 @@ struct TcOperand {
     int64_t plane_ld;
     int planes;
     int mn_major = 0;
+    int box_planes = 0;  // planes one TMA box copies (0 = all); SYR2K buffers hold two matrices
 };
 
 // Row stride and plane size (elements) of an operand written by the split
@@ -90,6 +91,16 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
                    const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
                    int* launches);
 
+// SYR2K (Section 6.1) on the tensor cores: the `uplo` (1 lower, 2 upper)
+// triangle of C (N x N) <- alpha (X Y^T + Y X^T) + beta C, X and Y the two
+// N x K operands stored in one buffer `xy`: planes [0, P) hold X, planes
+// [P, 2P) hold Y (P = 1 for nterms 1: hi; 2 for nterms 3: hi, lo), with
+// xy.planes = 2P and xy.box_planes = P.  Only tiles that meet the triangle
+// are computed and only triangle elements are stored.
+int launch_tc_syr2k(const TcOperand& xy, int nterms, int uplo, int64_t N, int64_t K, float alpha,
+                    float beta, float* C, int64_t ldc, const TcLaunch& cfg, int* err_word,
+                    int num_sms, cudaStream_t stream, int* launches);
+
 // FP32 SIMT GEMM (row-major, op by trans flags).
 cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
@@ -129,9 +140,17 @@ cudaError_t launch_split_grouped_t(const SplitJob* dev_jobs, const int* dev_tile
 cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,
                              int64_t ldx, uint16_t* out, int64_t ldo, cudaStream_t stream);
 
-// C <- beta * C (C <- 0 when beta == 0, without reading C).
+// C <- beta * C (C <- 0 when beta == 0, without reading C); uplo 1 / 2
+// restricts it to the lower / upper triangle (diagonal included).
 cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t ldc,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int uplo = 0);
+
+// SYR2K on the CUDA cores: the `uplo` (1 lower, 2 upper) triangle of C
+// (N x N) <- alpha (op(X) op(Y)^T + op(Y) op(X)^T) + beta C, op(X) = X
+// (stored N x K, trans 0) or X^T (stored K x N, trans 1).
+cudaError_t launch_simt_syr2k(int uplo, int trans, int64_t N, int64_t K, float alpha,
+                              const float* X, int64_t ldx, const float* Y, int64_t ldy, float beta,
+                              float* C, int64_t ldc, cudaStream_t stream);
 
 // C <- alpha * sum_s P[s] + beta * C over split_k dense M x N slabs.
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int split_k, const float* P, float alpha,

@@ -13,6 +13,12 @@
 //  * remainder tiles are zero-filled on load and stored element by element
 //    (Section 3.1, last paragraph), full tiles with 16-byte accesses.
 // All four op(A)/op(B) combinations are handled by the load index math.
+//
+// SYR2K (Section 6.1, UPLO 1 = lower / 2 = upper triangle): the same kernel
+// over the two GEMM updates of each C block.  The K loop runs over both
+// products, A-side rows of X with B-side rows of Y and then the reverse, each
+// half zero-padded to whole BK slices; blocks wholly outside the triangle
+// return at once and the epilogue stores only triangle elements.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -82,7 +88,7 @@ __device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const Frag& f)
     }
 }
 
-template <bool TA, bool TB, bool VEC>
+template <bool TA, bool TB, bool VEC, int UPLO>
 __global__ void __launch_bounds__(THREADS, 2)
     simt_f32_kernel(int M, int N, int K, float alpha, const float* __restrict__ A, int64_t lda,
                     const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C,
@@ -96,6 +102,8 @@ __global__ void __launch_bounds__(THREADS, 2)
 
     const int m0 = blockIdx.y * BM;
     const int n0 = blockIdx.x * BN;
+    if (UPLO == 1 && n0 > m0 + BM - 1) return;  // every column right of every row
+    if (UPLO == 2 && n0 + BN - 1 < m0) return;  // every column left of every row
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     const bool mn_full = (m0 + BM <= M) && (n0 + BN <= N);
@@ -106,10 +114,25 @@ __global__ void __launch_bounds__(THREADS, 2)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-    const int nk = (K + BK - 1) / BK;
+    const int nk1 = (K + BK - 1) / BK;  // slices of one product
+    const int nk = UPLO ? 2 * nk1 : nk1;
+    // slice kt: its K offset and the matrices feeding the A and B sides
+    auto slice = [&](int kt, const float*& xa, int64_t& lxa, const float*& xb, int64_t& lxb) {
+        const bool second = UPLO && kt >= nk1;
+        xa = second ? B : A;
+        lxa = second ? ldb : lda;
+        xb = second ? A : B;
+        lxb = second ? lda : ldb;
+        return (second ? kt - nk1 : kt) * BK;
+    };
     Frag fa, fb;
-    load_slice<A_KC, VEC>(A, lda, M, K, m0, 0, mn_full && BK <= K, fa);
-    load_slice<B_KC, VEC>(B, ldb, N, K, n0, 0, mn_full && BK <= K, fb);
+    {
+        const float *xa, *xb;
+        int64_t lxa, lxb;
+        const int k0 = slice(0, xa, lxa, xb, lxb);
+        load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, mn_full && BK <= K, fa);
+        load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, mn_full && BK <= K, fb);
+    }
     store_slice<A_KC>(As[0], fa);
     store_slice<B_KC>(Bs[0], fb);
     __syncthreads();
@@ -117,10 +140,12 @@ __global__ void __launch_bounds__(THREADS, 2)
     for (int kt = 0; kt < nk; ++kt) {
         const int cur = kt & 1;
         if (kt + 1 < nk) {
-            const int k0 = (kt + 1) * BK;
+            const float *xa, *xb;
+            int64_t lxa, lxb;
+            const int k0 = slice(kt + 1, xa, lxa, xb, lxb);
             const bool full = mn_full && (k0 + BK <= K);
-            load_slice<A_KC, VEC>(A, lda, M, K, m0, k0, full, fa);
-            load_slice<B_KC, VEC>(B, ldb, N, K, n0, k0, full, fb);
+            load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, full, fa);
+            load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, full, fb);
         }
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
@@ -154,7 +179,10 @@ __global__ void __launch_bounds__(THREADS, 2)
             float o[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) o[j] = alpha * acc[i][h * 4 + j];
-            if (c_vec && col + 4 <= N) {
+            // SYR2K: the 4-wide group is wholly inside the triangle, or is
+            // stored element by element
+            const bool whole = UPLO == 0 || (UPLO == 1 ? col + 3 <= row : col >= row);
+            if (c_vec && col + 4 <= N && whole) {
                 float4* p = reinterpret_cast<float4*>(crow + col);
                 if (beta != 0.0f) {
                     const float4 old = *p;
@@ -167,7 +195,8 @@ __global__ void __launch_bounds__(THREADS, 2)
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (col + j < N) {
+                    const bool in = UPLO == 0 || (UPLO == 1 ? col + j <= row : col + j >= row);
+                    if (col + j < N && in) {
                         float v = o[j];
                         if (beta != 0.0f) v = fmaf(beta, crow[col + j], v);
                         crow[col + j] = v;
@@ -178,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     }
 }
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, int UPLO = 0>
 cudaError_t launch_tt(int M, int N, int K, float alpha, const float* A, int64_t lda,
                       const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
                       cudaStream_t stream) {
@@ -187,15 +216,33 @@ cudaError_t launch_tt(int M, int N, int K, float alpha, const float* A, int64_t 
     const int c_vec = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     if (vec)
-        simt_f32_kernel<TA, TB, true><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda, B, ldb,
-                                                                    beta, C, ldc, c_vec);
+        simt_f32_kernel<TA, TB, true, UPLO><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda,
+                                                                          B, ldb, beta, C, ldc,
+                                                                          c_vec);
     else
-        simt_f32_kernel<TA, TB, false><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda, B,
-                                                                     ldb, beta, C, ldc, c_vec);
+        simt_f32_kernel<TA, TB, false, UPLO><<<grid, THREADS, 0, stream>>>(M, N, K, alpha, A, lda,
+                                                                           B, ldb, beta, C, ldc,
+                                                                           c_vec);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_simt_syr2k(int uplo, int trans, int64_t N, int64_t K, float alpha,
+                              const float* X, int64_t ldx, const float* Y, int64_t ldy, float beta,
+                              float* C, int64_t ldc, cudaStream_t stream) {
+    if ((N + BM - 1) / BM > 65535 || N > (1ll << 31) - BM || K > (1ll << 30) - BK)
+        return cudaErrorInvalidValue;
+    const int n = int(N), k = int(K);
+    // trans 0: X, Y stored N x K; the A side reads rows of X (K-contiguous)
+    // and the B side needs X^T, i.e. rows of the stored N x K matrix again
+    // (the "transposed B" load).  trans 1: X, Y stored K x N, the other way.
+    if (uplo == 1)
+        return trans ? launch_tt<true, false, 1>(n, n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream)
+                     : launch_tt<false, true, 1>(n, n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream);
+    return trans ? launch_tt<true, false, 2>(n, n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream)
+                 : launch_tt<false, true, 2>(n, n, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream);
+}
 
 cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta,

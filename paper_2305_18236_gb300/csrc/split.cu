@@ -6,7 +6,8 @@
 //    (lo = 0 where hi is not finite).  x - hi is exact in FP32, so hi + lo
 //    keeps x to within 2^-16 |x|.  The split is not in the paper.
 //  * pack_bf16: the same re-layout for BF16 inputs (no arithmetic).
-//  * scale_c: C <- beta * C, the K == 0 / alpha == 0 quick return.
+//  * scale_c: C <- beta * C, the K == 0 / alpha == 0 quick return (of a
+//    whole matrix, or of one triangle for SYR2K).
 //  * splitk_reduce: C <- alpha * sum_s P_s + beta * C over split-K partial
 //    sums, in increasing s (beta applied once, as in Algorithm 1).
 #include <cuda_bf16.h>
@@ -159,11 +160,12 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int64_t co
 }
 
 __global__ void __launch_bounds__(256) scale_c_kernel(int64_t M, int64_t N, float beta, float* C,
-                                                      int64_t ldc) {
+                                                      int64_t ldc, int uplo) {
     const int64_t total = M * N;
     for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
         const int64_t i = idx / N, j = idx - i * N;
+        if ((uplo == 1 && j > i) || (uplo == 2 && j < i)) continue;
         float* c = C + i * ldc + j;
         *c = beta == 0.0f ? 0.0f : beta * *c;
     }
@@ -443,9 +445,9 @@ cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16
 }
 
 cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t ldc,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int uplo) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    scale_c_kernel<<<grid_for(M * N, 256), 256, 0, stream>>>(M, N, beta, C, ldc);
+    scale_c_kernel<<<grid_for(M * N, 256), 256, 0, stream>>>(M, N, beta, C, ldc, uplo);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,14 @@ struct TcParams {
     int count;
     int c_tma;  // epilogue writes through the C tensor map (beta == 0 or split-K partials)
     int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
+    // SYR2K (single launches): uplo 1 = lower, 2 = upper triangle of C (0 =
+    // plain GEMM); syr_kb = K blocks of one product (the K loop runs twice as
+    // far: A-side rows then B-side rows); syr_plane = plane index where the
+    // second matrix's planes start in the shared operand buffer
+    int uplo;
+    int syr_kb;
+    int syr_plane;
+    int tri_r;  // BN / 128
 };
 
 template <int BN, int BK, int NTERMS>
@@ -111,6 +119,7 @@ struct EpiInfo {
     float alpha, beta;
     float* C;
     long long ldc;
+    int uplo;  // 1: store only col <= row, 2: only col >= row (SYR2K)
 };
 
 // Local tile index -> (m tile, n tile): groups of `g` M tiles are walked
@@ -124,11 +133,49 @@ __device__ __forceinline__ void raster(int t, int num_m, int num_n, int g, int& 
     nt = r / gm;
 }
 
+// SYR2K tile space: only the 128 x BN tiles that meet the stored triangle,
+// row of tiles by row of tiles.  With r = BN / 128, tile row mt needs the
+// column tiles nt <= mt / r (lower) or nt >= mt / r (upper), so the number
+// of tiles in rows 0 .. m-1 is F(m) + m (lower) or m * num_n - F(m)
+// (upper), F(m) = sum_{i<m} floor(i / r).
+__device__ __forceinline__ int tri_floor_sum(int m, int r) {
+    if (r == 1) return m * (m - 1) / 2;
+    const int q = m >> 1;
+    return q * (q - 1) + ((m & 1) ? q : 0);
+}
+
+__device__ __forceinline__ int tri_tiles_before(int m, int r, int uplo, int num_n) {
+    return uplo == 1 ? tri_floor_sum(m, r) + m : m * num_n - tri_floor_sum(m, r);
+}
+
+__device__ __forceinline__ void tri_tile(int t, int num_m, int num_n, int r, int uplo, int& mt,
+                                         int& nt) {
+    int lo = 0, hi = num_m;  // tiles_before(lo) <= t < tiles_before(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tri_tiles_before(mid, r, uplo, num_n) <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    mt = lo;
+    nt = t - tri_tiles_before(lo, r, uplo, num_n) + (uplo == 1 ? 0 : lo / r);
+}
+
 template <bool GROUPED>
 __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUtensorMap* tmA,
                                              const CUtensorMap* tmB) {
     TileInfo ti;
-    if (!GROUPED) {
+    if (!GROUPED && p.uplo) {
+        ti.ks = 0;
+        tri_tile(t, p.num_m, p.num_n, p.tri_r, p.uplo, ti.mt, ti.nt);
+        ti.kb0 = 0;
+        ti.kb1 = p.k_blocks;
+        ti.prob = 0;
+        ti.maj = p.maj;
+        ti.ma = tmA;
+        ti.mb = tmB;
+    } else if (!GROUPED) {
         const int per_split = p.num_m * p.num_n;
         ti.ks = t / per_split;
         raster(t - ti.ks * per_split, p.num_m, p.num_n, p.raster_group, ti.mt, ti.nt);
@@ -173,6 +220,7 @@ __device__ __forceinline__ EpiInfo get_epi(int prob, int ks, const TcParams& p) 
             e.C = p.C;
             e.ldc = p.ldc;
         }
+        e.uplo = p.uplo;
     } else {
         const GroupedProblem* q = p.problems + prob;
         e.M = __ldg(&q->M);
@@ -181,6 +229,7 @@ __device__ __forceinline__ EpiInfo get_epi(int prob, int ks, const TcParams& p) 
         e.beta = __ldg(&q->beta);
         e.C = q->C;
         e.ldc = __ldg(&q->ldc);
+        e.uplo = 0;
     }
     return e;
 }
@@ -191,14 +240,17 @@ __device__ __forceinline__ EpiInfo get_epi(int prob, int ks, const TcParams& p) 
 // the warp writes row (row0 + rr), 32 consecutive columns, one per lane.
 // Reads of C are issued eight at a time so that their latencies overlap.
 // Split-K stores raw FP32 partial sums; otherwise C = alpha*v + beta*C
-// (C not read when beta == 0).
+// (C not read when beta == 0).  SYR2K (e.uplo) stores only the elements of
+// its triangle: lane `col` keeps the piece rows [rlo, rhi).
 __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0, int col0,
                                             const EpiInfo& e, int lane) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
     __syncwarp();
     const int col = col0 + lane;
-    const int rows = min(32, e.M - row0);
+    int rlo = 0, rhi = min(32, e.M - row0);
+    if (e.uplo == 1) rlo = max(0, col - row0);           // col <= row
+    if (e.uplo == 2) rhi = min(rhi, col - row0 + 1);      // col >= row
     if (col < e.N) {
         float* base = e.C + size_t(row0) * size_t(e.ldc) + col;
         const size_t ldc = size_t(e.ldc);
@@ -207,17 +259,18 @@ __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0
             for (int r0 = 0; r0 < 32; r0 += 8) {
                 float old[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) old[i] = r0 + i < rows ? base[(r0 + i) * ldc] : 0.0f;
+                for (int i = 0; i < 8; ++i)
+                    old[i] = (r0 + i >= rlo && r0 + i < rhi) ? base[(r0 + i) * ldc] : 0.0f;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    if (r0 + i < rows)
+                    if (r0 + i >= rlo && r0 + i < rhi)
                         base[(r0 + i) * ldc] =
                             fmaf(e.beta, old[i], e.alpha * stg[(r0 + i) * 33 + lane]);
             }
         } else {
 #pragma unroll 8
             for (int rr = 0; rr < 32; ++rr)
-                if (rr < rows) base[rr * ldc] = e.alpha * stg[rr * 33 + lane];
+                if (rr >= rlo && rr < rhi) base[rr * ldc] = e.alpha * stg[rr * 33 + lane];
         }
     }
     __syncwarp();
@@ -301,14 +354,16 @@ __device__ __forceinline__ OpLayout op_layout(int mn, int plane_bytes) {
 // TMA copies of one operand's BK-deep slice into a stage: one box for a
 // K-major operand, rows / 64 boxes for an MN-major one.  x coordinates are
 // multiples of BK or of 64 elements (16-byte aligned) and never negative.
+// `plane` is the first plane copied (0, or where the second matrix of a
+// SYR2K operand buffer starts).
 __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* map, uint64_t* bar,
                                              int mn, int rows, int group_bytes, int kcoord,
-                                             int row0, uint64_t pol) {
+                                             int row0, int plane, uint64_t pol) {
     if (!mn) {
-        tma_load_3d(dst, map, bar, kcoord, row0, 0, pol);
+        tma_load_3d(dst, map, bar, kcoord, row0, plane, pol);
     } else {
         for (int g = 0; g < rows / 64; ++g)
-            tma_load_3d(dst + g * group_bytes, map, bar, row0 + g * 64, kcoord, 0, pol);
+            tma_load_3d(dst + g * group_bytes, map, bar, row0 + g * 64, kcoord, plane, pol);
     }
 }
 
@@ -377,12 +432,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
+                    // SYR2K: K blocks [0, syr_kb) pair A-side rows of the first
+                    // matrix with B-side rows of the second, the next syr_kb
+                    // blocks the other way round (the two GEMM updates of a block)
+                    int kc = kb, za = 0, zb = 0;
+                    if (!GROUPED && p.syr_kb > 0) {
+                        const int second = kb >= p.syr_kb;
+                        kc = kb - (second ? p.syr_kb : 0);
+                        za = second ? p.syr_plane : 0;
+                        zb = second ? 0 : p.syr_plane;
+                    }
                     uint8_t* st = smem + s * S::STAGE;
                     mbar_arrive_expect_tx(&full[s], S::STAGE);
-                    load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kb * BK,
-                                 ti.mt * kBM, pol);
+                    load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kc * BK,
+                                 ti.mt * kBM, za, pol);
                     load_operand(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], (ti.maj >> 1) & 1,
-                                 BN, S::MN_GROUP, kb * BK, ti.nt * BN, pol);
+                                 BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol);
                     filled |= 1u << s;
                     fill_par = (fill_par & ~(1u << s)) | (ph << s);
                 }
@@ -1020,7 +1085,7 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
     cuuint64_t strides[2] = {cuuint64_t(op.ld) * 2,
                              cuuint64_t(op.planes > 1 ? op.plane_ld : op.ld * stored_rows) * 2};
     cuuint32_t box[3] = {cuuint32_t(op.mn_major ? 64 : bk), cuuint32_t(op.mn_major ? bk : box_rows),
-                         cuuint32_t(op.planes)};
+                         cuuint32_t(op.box_planes > 0 ? op.box_planes : op.planes)};
     cuuint32_t estr[3] = {1, 1, 1};
     const bool sw128 = op.mn_major || bk * 2 == 128;
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(op.base), dims,
@@ -1089,6 +1154,51 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
         ++n;
     }
     if (launches) *launches += n;
+    return 0;
+}
+
+int launch_tc_syr2k(const TcOperand& xy, int nterms, int uplo, int64_t N, int64_t K, float alpha,
+                    float beta, float* C, int64_t ldc, const TcLaunch& cfg, int* err_word,
+                    int num_sms, cudaStream_t stream, int* launches) {
+    const int P = nterms == 1 ? 1 : 2;
+    if (uplo != 1 && uplo != 2) return -1;
+    if (xy.planes != 2 * P || xy.box_planes != P) return -1;
+    if (N > (1ll << 31) - 256 || K > (1ll << 30) - 256) return -6;
+    const int bn = cfg.bn == 128 ? 128 : 256;
+    const int bk = cfg.bk == 64 ? 64 : 32;
+    TcParams p{};
+    p.M = int(N);
+    p.N = int(N);
+    p.K = int(K);
+    p.alpha = alpha;
+    p.beta = beta;
+    p.C = C;
+    p.ldc = ldc;
+    p.num_m = int((N + kBM - 1) / kBM);
+    p.num_n = int((N + bn - 1) / bn);
+    p.syr_kb = int((K + bk - 1) / bk);
+    p.k_blocks = 2 * p.syr_kb;
+    p.kb_per_split = p.k_blocks;
+    p.split_k = 1;
+    p.uplo = uplo;
+    p.syr_plane = P;
+    p.tri_r = bn / kBM;
+    // tiles meeting the triangle (host copy of the kernel's tri_tiles_before(num_m))
+    const int64_t r = p.tri_r, m = p.num_m;
+    const int64_t q = m / 2;
+    const int64_t fsum = r == 1 ? m * (m - 1) / 2 : q * (q - 1) + ((m & 1) ? q : 0);
+    const int64_t tiles = uplo == 1 ? fsum + m : m * p.num_n - fsum;
+    if (tiles > (1ll << 31) - 1) return -6;
+    p.num_tiles = int(tiles);
+    p.maj = xy.mn_major ? 3 : 0;
+    fill_common(p, cfg, bk, nterms, err_word);
+    CUtensorMap ta, tb, tc{};
+    if (!encode_operand(&ta, xy, bk, kBM) || !encode_operand(&tb, xy, bk, bn)) return -4;
+    p.c_tma = 0;  // diagonal tiles store only their triangle
+    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    const int rc = dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream);
+    if (rc != 0) return rc;
+    if (launches) *launches += 1;
     return 0;
 }
 

@@ -156,6 +156,28 @@ def matmul(A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False, mode="
     return C
 
 
+def syr2k(A, B, C=None, alpha=1.0, beta=0.0, uplo="lower", trans=False, mode="bf16x3", h=None):
+    """SYR2K (Section 6.1): the ``uplo`` triangle of C <- alpha (A B^T + B A^T)
+    + beta C for float32 CUDA tensors A, B of shape (N, K), or alpha (A^T B +
+    B^T A) + beta C for shape (K, N) with ``trans``.  The other triangle of C
+    is left as it is (uninitialised when C is None)."""
+    if A.dtype != torch.float32 or B.dtype != torch.float32:
+        raise TypeError("float32 inputs expected")
+    if tuple(A.shape) != tuple(B.shape):
+        raise ValueError("A and B must have the same shape")
+    h = h or handle(A.device)
+    N, K = (A.size(1), A.size(0)) if trans else (A.size(0), A.size(1))
+    C = _out(C, N, N, beta, A.device)
+    m = _mode(mode)
+    h.ensure_workspace(h.lib.gemm_syr2k_workspace_size(h.h, m, int(trans), N, K))
+    st = h.lib.gemm_syr2k(h.h, _lib.UPLOS[uplo], int(trans), N, K, float(alpha),
+                          ctypes.c_void_p(A.data_ptr()), _ld(A), ctypes.c_void_p(B.data_ptr()),
+                          _ld(B), float(beta), ctypes.c_void_p(C.data_ptr()), _ld(C), m,
+                          _stream(A.device))
+    check(st, "gemm_syr2k", h.h)
+    return C
+
+
 def matmul_bf16(A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False, h=None):
     """C = alpha * op(A) @ op(B) + beta * C for bfloat16 A, B and float32 C."""
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
