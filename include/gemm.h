@@ -178,11 +178,13 @@ gemm_status_t gemm_split_bf16(gemm_handle_t handle, gemm_op_t trans, int64_t row
 
 /* gemm() on HOST buffers: copies A, B (and C when beta != 0) to device
  * buffers the handle owns (grown with cudaMalloc on demand), computes, copies
- * C back and synchronises `stream`.  B is copied (and split) first; then up
- * to four row blocks of op(A) and C are each copied in, multiplied and copied
- * out on two streams the handle owns, so the copies of one block overlap the
- * GEMM of its neighbours.  Pinned host memory gives asynchronous, overlapped
- * copies; pageable memory works but is slower.  Also reports a kernel's
+ * C back and synchronises `stream`.  A three-stream pipeline the handle owns
+ * runs over up to sixteen row blocks of op(A) and C (of at least 512 rows):
+ * one stream copies B and then every block's A and C rows in back to back,
+ * one splits and multiplies each block as its rows arrive, one copies each
+ * block's C out as soon as it is done, so the host link stays busy in both
+ * directions.  Pinned host memory gives asynchronous, overlapped copies;
+ * pageable memory works but is slower.  Also reports a kernel's
  * bounded-wait expiry (GEMM_ERR_TIMEOUT).  Positions as for gemm(). */
 gemm_status_t gemm_from_host(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                              int64_t M, int64_t N, int64_t K,
@@ -228,8 +230,10 @@ enum {
  * the launch configuration.  With GEMM_GROUPED_AUTOTUNE the configurations a
  * shared-memory / tensor-memory feasibility model admits are ranked by a cost
  * model (padded tile work x wave quantisation), the best few are timed on the
- * problems themselves -- writing only to plan-owned scratch, never to any
- * C -- and the fastest is kept; results are cached per process (and in the
+ * problems themselves -- all of them when their outputs fit in scratch of
+ * up to 4 GB and a quarter of the free device memory, else the leading ones
+ * that do; writing only to that plan-owned scratch, never to any C -- and
+ * the fastest is kept; results are cached per process (and in the
  * file named by the GEMM_AUTOTUNE_CACHE environment variable, if set) keyed
  * by SM count, mode and problem shapes.  Tuning runs on `stream` and
  * synchronises it.  Without it, the handle's configuration is used.  The
@@ -248,7 +252,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t handle, gemm_mode_t mode,
 gemm_status_t gemm_grouped_plan_run(gemm_grouped_plan_t plan, void *stream);
 
 /* The configuration the plan launches with, and the tuned time of one
- * tensor-core launch on the tuning subset in ms (0 if not tuned). */
+ * tensor-core launch on the tuning set in ms (0 if not tuned). */
 gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t plan, gemm_config_t *cfg,
                                        double *tuned_ms);
 

@@ -14,6 +14,9 @@
 #include "../../include/gemm.h"
 #include "internal.h"
 
+// Row blocks of the gemm_from_host pipeline (at most; blocks of >= 512 rows).
+constexpr int kPipeBlocks = 16;
+
 struct gemm_context {
     int device = 0;
     int num_sms = 0;
@@ -30,8 +33,10 @@ struct gemm_context {
     float* hB = nullptr;
     float* hC = nullptr;
     size_t hA_bytes = 0, hB_bytes = 0, hC_bytes = 0;
-    cudaStream_t pipe[2] = {nullptr, nullptr};  // gemm_from_host row-block streams
-    cudaEvent_t pipe_ev[3] = {nullptr, nullptr, nullptr};
+    // gemm_from_host pipeline: copy-in, compute and copy-out streams; events
+    // start, B ready, end, then per block "inputs in" and "product done"
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t pipe_ev[3 + 2 * kPipeBlocks] = {};
     // benchmark hook: event pairs around main kernels
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;  // 2 per recorded launch
@@ -548,18 +553,22 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     const int64_t br = transB ? N : K, bc = transB ? K : N;
     if ((st = grow(&h->hA, &h->hA_bytes, size_t(ar) * lda * 4)) != GEMM_OK) return st;
     if ((st = grow(&h->hB, &h->hB_bytes, size_t(br) * ldb * 4)) != GEMM_OK) return st;
-    for (int i = 0; i < 2; ++i)
-        if (!h->pipe[i] && cudaStreamCreateWithFlags(&h->pipe[i], cudaStreamNonBlocking) != cudaSuccess)
+    for (cudaStream_t& q : h->pipe)
+        if (!q && cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess)
             return GEMM_ERR_CUDA;
-    for (int i = 0; i < 3; ++i)
-        if (!h->pipe_ev[i] && cudaEventCreateWithFlags(&h->pipe_ev[i], cudaEventDisableTiming) !=
-                                  cudaSuccess)
+    for (cudaEvent_t& e : h->pipe_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return GEMM_ERR_CUDA;
 
-    // Row blocks of op(A) and C: block i is copied in, computed and copied
-    // out on stream pipe[i % 2], so the copies of one block overlap the
-    // GEMM of its neighbours.  B is copied (and split) once, first.
-    const int nb = int(std::min<int64_t>(4, std::max<int64_t>(1, M / 1024)));
+    // Three-stage pipeline over row blocks of op(A) and C, one stream per
+    // stage so that no stage waits behind another in stream order:
+    //   copy-in  (pipe[0]): B, then A_i and C_i of every block back to back;
+    //   compute  (pipe[1]): split B, then per block split A_i and multiply;
+    //   copy-out (pipe[2]): C_i as soon as its product is done.
+    // The host link then stays busy from the first byte, C_i travels back
+    // while later blocks travel in, and only the last block's product and
+    // copy-out follow the last input byte.
+    const int nb = int(std::min<int64_t>(kPipeBlocks, std::max<int64_t>(1, M / 512)));
     const int64_t rb = ((M + nb - 1) / nb + 127) / 128 * 128;
     const bool tc = mode != GEMM_MODE_F32_SIMT;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
@@ -576,61 +585,77 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     }
     uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
     uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
+    cudaStream_t s_in = h->pipe[0], s_mm = h->pipe[1], s_out = h->pipe[2];
+    cudaEvent_t ev_start = h->pipe_ev[0], ev_b = h->pipe_ev[1], ev_end = h->pipe_ev[2];
+    cudaEvent_t* ev_in = h->pipe_ev + 3;               // [kPipeBlocks]
+    cudaEvent_t* ev_done = h->pipe_ev + 3 + kPipeBlocks;  // [kPipeBlocks]
     int launches = 0;
-    if (cudaMemcpy2DAsync(h->hB, ldb * 4, B, ldb * 4, bc * 4, br, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
+    // everything earlier on the caller's stream comes first
+    if (cudaEventRecord(ev_start, s) != cudaSuccess ||
+        cudaStreamWaitEvent(s_in, ev_start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s_mm, ev_start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(s_out, ev_start, 0) != cudaSuccess)
+        return GEMM_ERR_CUDA;
+    if (cudaMemcpy2DAsync(h->hB, ldb * 4, B, ldb * 4, bc * 4, br, cudaMemcpyHostToDevice, s_in) !=
+            cudaSuccess ||
+        cudaEventRecord(ev_b, s_in) != cudaSuccess || cudaStreamWaitEvent(s_mm, ev_b, 0) != cudaSuccess)
         return GEMM_ERR_CUDA;
     if (tc) {
-        if (split_op(pb, N, K, h->hB, ldb, b_hi, planes, s) != cudaSuccess) return GEMM_ERR_CUDA;
+        if (split_op(pb, N, K, h->hB, ldb, b_hi, planes, s_mm) != cudaSuccess) return GEMM_ERR_CUDA;
         ++launches;
     }
-    if (cudaEventRecord(h->pipe_ev[0], s) != cudaSuccess) return GEMM_ERR_CUDA;
     for (int i = 0; i < nb; ++i) {
         const int64_t r0 = i * rb;
         if (r0 >= M) break;
         const int64_t rows = std::min(rb, M - r0);
-        cudaStream_t si = h->pipe[i & 1];
-        if (cudaStreamWaitEvent(si, h->pipe_ev[0], 0) != cudaSuccess) return GEMM_ERR_CUDA;
-        // rows r0.. of op(A): stored rows of A, or stored columns when transposed
+        // copy-in: rows r0.. of op(A) (stored rows of A, or stored columns
+        // when transposed) and of C
         const size_t aoff = transA ? size_t(r0) : size_t(r0) * lda;
         const cudaError_t ce =
             transA ? cudaMemcpy2DAsync(h->hA + aoff, lda * 4, A + aoff, lda * 4, rows * 4, K,
-                                       cudaMemcpyHostToDevice, si)
+                                       cudaMemcpyHostToDevice, s_in)
                    : cudaMemcpy2DAsync(h->hA + aoff, lda * 4, A + aoff, lda * 4, K * 4, rows,
-                                       cudaMemcpyHostToDevice, si);
+                                       cudaMemcpyHostToDevice, s_in);
         if (ce != cudaSuccess) return GEMM_ERR_CUDA;
         float* cblk = h->hC + size_t(r0) * ldc;
         if (beta != 0.0f && cudaMemcpy2DAsync(cblk, ldc * 4, C + size_t(r0) * ldc, ldc * 4, N * 4,
-                                              rows, cudaMemcpyHostToDevice, si) != cudaSuccess)
+                                              rows, cudaMemcpyHostToDevice, s_in) != cudaSuccess)
             return GEMM_ERR_CUDA;
+        if (cudaEventRecord(ev_in[i], s_in) != cudaSuccess ||
+            cudaStreamWaitEvent(s_mm, ev_in[i], 0) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        // compute
         if (tc) {
             // the block's rows inside the packed A: packed rows (K-major) or
             // columns (MN-major; r0 is a multiple of 128, so 16-byte aligned)
             uint16_t* ablk = a_hi + (pa.mn ? r0 : r0 * pa.lay.ld);
-            if (split_op(pa, rows, K, h->hA + aoff, lda, ablk, planes, si) != cudaSuccess)
+            if (split_op(pa, rows, K, h->hA + aoff, lda, ablk, planes, s_mm) != cudaSuccess)
                 return GEMM_ERR_CUDA;
             const TcOperand oa = operand_of(pa, ablk, rows, K, planes);
             const TcOperand ob = operand_of(pb, b_hi, N, K, planes);
             int n = 0;
             const int rc = gb300::launch_tc_gemm(oa, ob, nterms, rows, N, K, alpha, beta, cblk, ldc,
-                                                 nullptr, cfg, h->err_word, h->num_sms, si, &n);
+                                                 nullptr, cfg, h->err_word, h->num_sms, s_mm, &n);
             if (rc != 0) return static_cast<gemm_status_t>(rc);
             launches += 1 + n;
         } else {
             if (gb300::launch_simt_f32(transA, transB, rows, N, K, alpha, h->hA + aoff, lda, h->hB,
-                                       ldb, beta, cblk, ldc, si) != cudaSuccess)
+                                       ldb, beta, cblk, ldc, s_mm) != cudaSuccess)
                 return GEMM_ERR_CUDA;
             ++launches;
         }
-        if (cudaMemcpy2DAsync(C + size_t(r0) * ldc, ldc * 4, cblk, ldc * 4, N * 4, rows,
-                              cudaMemcpyDeviceToHost, si) != cudaSuccess)
+        // copy-out
+        if (cudaEventRecord(ev_done[i], s_mm) != cudaSuccess ||
+            cudaStreamWaitEvent(s_out, ev_done[i], 0) != cudaSuccess ||
+            cudaMemcpy2DAsync(C + size_t(r0) * ldc, ldc * 4, cblk, ldc * 4, N * 4, rows,
+                              cudaMemcpyDeviceToHost, s_out) != cudaSuccess)
             return GEMM_ERR_CUDA;
     }
-    // join both block streams back into the caller's stream
-    for (int i = 0; i < 2; ++i)
-        if (cudaEventRecord(h->pipe_ev[1 + i], h->pipe[i]) != cudaSuccess ||
-            cudaStreamWaitEvent(s, h->pipe_ev[1 + i], 0) != cudaSuccess)
-            return GEMM_ERR_CUDA;
+    // the copy-out stream ends after every product (it waited on each) and
+    // every product after its inputs: joining it joins the whole pipeline
+    if (cudaEventRecord(ev_end, s_out) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ev_end, 0) != cudaSuccess)
+        return GEMM_ERR_CUDA;
     st = gemm_sync(h, stream);
     h->last_launches = launches;
     return st;

@@ -464,12 +464,22 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
                 free_plan(p);
                 return GEMM_ERR_CUDA;
             }
-            // tune on the leading problems whose outputs fit in 512 MB of scratch
+            // Tune on the whole problem set when its outputs fit in scratch of at
+            // most 4 GB and a quarter of the free device memory (the wave count
+            // of the persistent grid, which the timing must see, depends on the
+            // whole set); otherwise on the leading problems that fit.
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+                cudaGetLastError();
+                free_b = 0;
+            }
+            const size_t tune_cap =
+                std::max<size_t>(size_t(512) << 20, std::min<size_t>(size_t(4) << 30, free_b / 4));
             std::vector<HostProb> sub;
             size_t cbytes = 0;
             for (const HostProb& q : ps) {
                 const size_t b = round256(size_t(q.M) * q.N * 4);
-                if (!sub.empty() && cbytes + b > (size_t(512) << 20)) break;
+                if (!sub.empty() && cbytes + b > tune_cap) break;
                 sub.push_back(q);
                 cbytes += b;
             }
