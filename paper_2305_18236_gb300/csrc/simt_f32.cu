@@ -57,18 +57,23 @@ __device__ __forceinline__ void load_slice(const float* __restrict__ X, int64_t 
             for (int q = 0; q < 8; ++q) f.v[q] = (r < R && k + q < K) ? __ldg(p + q) : 0.0f;
         }
     } else {
-        // thread -> k0 + (t >> 4), rows r0 + (t & 15) * 8 .. +7
-        const int k = k0 + (t >> 4);
-        const int r = r0 + (t & 15) * 8;
+        // thread -> k0 + (t >> 5) and k0 + (t >> 5) + 8, rows r0 + (t & 31) * 4 .. +3:
+        // a warp reads one 512-byte row segment per instruction
+        const int k = k0 + (t >> 5);
+        const int r = r0 + (t & 31) * 4;
         const float* p = X + int64_t(k) * ldx + r;
+        const float* p8 = p + 8 * ldx;
         if (VEC && full) {
             const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-            const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+            const float4 b = __ldg(reinterpret_cast<const float4*>(p8));
             f.v[0] = a.x; f.v[1] = a.y; f.v[2] = a.z; f.v[3] = a.w;
             f.v[4] = b.x; f.v[5] = b.y; f.v[6] = b.z; f.v[7] = b.w;
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) f.v[q] = (k < K && r + q < R) ? __ldg(p + q) : 0.0f;
+            for (int q = 0; q < 4; ++q) {
+                f.v[q] = (k < K && r + q < R) ? __ldg(p + q) : 0.0f;
+                f.v[4 + q] = (k + 8 < K && r + q < R) ? __ldg(p8 + q) : 0.0f;
+            }
         }
     }
 }
@@ -82,9 +87,9 @@ __device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const Frag& f)
 #pragma unroll
         for (int q = 0; q < 8; ++q) S[k + q][r] = f.v[q];
     } else {
-        const int k = t >> 4, r = (t & 15) * 8;
+        const int k = t >> 5, r = (t & 31) * 4;
         *reinterpret_cast<float4*>(&S[k][r]) = make_float4(f.v[0], f.v[1], f.v[2], f.v[3]);
-        *reinterpret_cast<float4*>(&S[k][r + 4]) = make_float4(f.v[4], f.v[5], f.v[6], f.v[7]);
+        *reinterpret_cast<float4*>(&S[k + 8][r]) = make_float4(f.v[4], f.v[5], f.v[6], f.v[7]);
     }
 }
 
