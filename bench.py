@@ -47,9 +47,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-compare", action="store_true", help="skip the FP32 SIMT comparison")
     p.add_argument("--e2e-steps", type=int, default=10)
-    p.add_argument("--operand-layout", default="as_stored", choices=["as_stored", "k_major"],
-                   help="as_stored: operands stored K x rows are split without transposing and "
-                        "read as MN-major tiles; k_major: every operand made K-contiguous first")
+    p.add_argument("--operand-layout", default="auto", choices=["auto", "as_stored", "k_major"],
+                   help="auto: library choice; as_stored: operands stored K x rows are split "
+                        "without transposing and read as MN-major tiles; k_major: every operand "
+                        "made K-contiguous first")
     p.add_argument("--workload", default="square",
                    choices=["square", "rect", "grouped", "chain", "syr2k"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "

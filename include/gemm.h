@@ -85,17 +85,29 @@ typedef struct gemm_context *gemm_handle_t;
  *    accumulation rounds toward zero, so long chains lose accuracy).
  *  cta_group: 1 = one CTA per 128-row tile; 2 = CTA pairs (a cluster of two
  *    SMs shares a 256-row tile, each staging half of B; bn must be 256);
- *    0 = library choice.
+ *    0 = library choice: pairs for GEMM_MODE_BF16X3 in gemm(),
+ *    gemm_from_host and gemm_backward when the problem has at least as many
+ *    256 x 256 tiles as the GPU has SM pairs, else one CTA per tile (grouped
+ *    launches and gemm_syr2k always use one CTA per tile).  bk 0 = 64, or
+ *    32 for GEMM_MODE_BF16X3 with one CTA per tile.
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
  *    the device error word and exits cleanly (0 = default, about seconds).
- *  operand_layout: GEMM_LAYOUT_AS_STORED (0, default): each operand reaches
- *    the tensor cores in its stored orientation -- A stored K x M (transA ==
- *    T) and B stored K x N (transB == N) are split without transposing and
- *    read as MN-major tiles, and gemm_bf16 reads every operand in place;
- *    GEMM_LAYOUT_K_MAJOR (1): every operand is made K-contiguous first (a
- *    transposing split, or a pack pass in gemm_bf16).  CTA pairs always use
- *    K-major tiles. */
-typedef enum { GEMM_LAYOUT_AS_STORED = 0, GEMM_LAYOUT_K_MAJOR = 1 } gemm_layout_t;
+ *  operand_layout: GEMM_LAYOUT_K_MAJOR (1): every operand is made
+ *    K-contiguous first (a transposing split, or a pack pass in gemm_bf16);
+ *    GEMM_LAYOUT_AS_STORED (2): each operand reaches the tensor cores in its
+ *    stored orientation -- A stored K x M (transA == T) and B stored K x N
+ *    (transB == N) are split without transposing and read as MN-major tiles,
+ *    and gemm_bf16 reads every operand in place; GEMM_LAYOUT_AUTO (0,
+ *    default): K-major in gemm(), gemm_from_host and gemm_backward (the
+ *    K-major kernel is a few percent faster and the split transposes at
+ *    nearly the copy rate), as stored in grouped plans and gemm_syr2k, and
+ *    in gemm_bf16 K-major only when the pack pass costs under a tenth of the
+ *    GEMM (large, compute-bound shapes) -- as stored otherwise. */
+typedef enum {
+    GEMM_LAYOUT_AUTO = 0,
+    GEMM_LAYOUT_K_MAJOR = 1,
+    GEMM_LAYOUT_AS_STORED = 2
+} gemm_layout_t;
 
 typedef struct {
     int32_t bn;
@@ -153,13 +165,13 @@ gemm_status_t gemm(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                    gemm_mode_t mode, void *stream);
 
 /* C <- alpha * op(A) op(B) + beta * C with BF16 A and B (uint16_t bit
- * patterns), FP32 C, tensor cores with FP32 accumulation.  Operands are read
- * in place by TMA in their stored orientation (K-contiguous, or MN-contiguous
- * for A stored K x M and B stored K x N) and need a 16-byte aligned base and
- * ld % 8 == 0 (else GEMM_ERR_ALIGN).  With operand_layout ==
- * GEMM_LAYOUT_K_MAJOR (or CTA pairs) the MN-contiguous operands are instead
- * packed K-contiguous into workspace first (Algorithm 1's pack step) and may
- * have any ld.  Argument positions as for gemm() (no mode; 15 is stream). */
+ * patterns), FP32 C, tensor cores with FP32 accumulation.  K-contiguous
+ * operands (A stored M x K, B stored N x K) are always read in place by TMA
+ * and need a 16-byte aligned base and ld % 8 == 0 (else GEMM_ERR_ALIGN).
+ * MN-contiguous ones (A stored K x M, B stored K x N) are either read in
+ * place as MN-major tiles (same alignment rule) or first packed K-contiguous
+ * into workspace (Algorithm 1's pack step; any ld), as operand_layout says
+ * (library choice: packed when the pass costs under a tenth of the GEMM).  Argument positions as for gemm() (no mode; 15 is stream). */
 gemm_status_t gemm_bf16(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                         int64_t M, int64_t N, int64_t K,
                         float alpha, const uint16_t *A, int64_t lda,

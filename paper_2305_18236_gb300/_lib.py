@@ -17,8 +17,8 @@ MODES = {"f32_simt": MODE_F32_SIMT, "simt": MODE_F32_SIMT, "bf16": MODE_BF16,
 
 LOWER, UPPER = 0, 1
 UPLOS = {"lower": LOWER, "upper": UPPER}
-LAYOUT_AS_STORED, LAYOUT_K_MAJOR = 0, 1
-LAYOUTS = {"as_stored": LAYOUT_AS_STORED, "k_major": LAYOUT_K_MAJOR}
+LAYOUT_AUTO, LAYOUT_K_MAJOR, LAYOUT_AS_STORED = 0, 1, 2
+LAYOUTS = {"auto": LAYOUT_AUTO, "k_major": LAYOUT_K_MAJOR, "as_stored": LAYOUT_AS_STORED}
 
 GEMM_OK = 0
 GEMM_ERR_ARG = -1

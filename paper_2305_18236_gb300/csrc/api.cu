@@ -60,18 +60,66 @@ gemm_status_t fail_arg(gemm_context* h, int pos) {
 // Stored-matrix geometry check: rows x cols stored with row stride ld.
 bool ld_ok(int64_t ld, int64_t cols) { return ld >= std::max<int64_t>(1, cols); }
 
-TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K) {
+// What a tensor-core launch serves (its library-choice defaults differ).
+enum class Call {
+    Split,    // gemm(), gemm_from_host, gemm_backward: FP32 operands split first
+    Bf16,     // gemm_bf16: BF16 operands, read in place or packed
+    Grouped,  // grouped plans (one CTA per tile)
+    Syr2k,    // gemm_syr2k (one CTA per tile)
+};
+
+// True when packing the MN-contiguous BF16 operands K-contiguous costs less
+// than a tenth of the GEMM itself (time estimates at rough GB300 rates): the
+// K-major kernel is then faster overall; otherwise they are read in place.
+bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
+    const double m = double(M), n = double(N), k = double(K);
+    const double t_mma = 2.0 * m * n * k / 1.2e15;
+    const double t_mem = (2.0 * (m * k + n * k) + 4.0 * m * n) / 6.0e12;
+    const double packed = (pack_a ? m * k : 0.0) + (pack_b ? n * k : 0.0);
+    return 4.0 * packed / 6.0e12 < 0.1 * std::max(t_mma, t_mem);
+}
+
+// Tile plan of one tensor-core launch.  Library choice (configuration 0):
+//  * split precision on split operands: CTA pairs (256 x 256 tiles,
+//    cta_group::2, BK 64) when there are at least as many pair tiles as SM
+//    pairs, since each SM then stages half of B and runs ~12 % fewer cycles
+//    per GEMM; one CTA per 128 x 256 tile (BK 32) otherwise.  Plain BF16 runs
+//    one CTA per tile (BK 64), which measured faster than pairs;
+//  * operands K-major for split operands (the split transposes at nearly the
+//    copy rate and the K-major kernel runs a few % faster) and for gemm_bf16
+//    when packing pays (pack_pays); in their stored orientation otherwise,
+//    and always in grouped plans and SYR2K, whose transposing passes cost
+//    more than the kernel gains.
+TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K, Call call,
+                 bool pack_a = false, bool pack_b = false) {
     TcLaunch c;
     c.bn = h->cfg.bn ? h->cfg.bn : 256;
-    c.bk = h->cfg.bk ? h->cfg.bk : (nterms == 3 ? 32 : 64);
+    const bool one_cta_only = call == Call::Grouped || call == Call::Syr2k;
+    if (one_cta_only) {
+        c.cta_group = 1;
+    } else if (h->cfg.cta_group != 0) {
+        c.cta_group = h->cfg.cta_group;
+    } else {
+        const int64_t pair_tiles = ((M + 255) / 256) * ((N + 255) / 256);
+        c.cta_group = (nterms == 3 && call == Call::Split && c.bn == 256 &&
+                       h->cfg.split_k <= 1 && pair_tiles >= h->num_sms / 2)
+                          ? 2
+                          : 1;
+    }
+    c.bk = h->cfg.bk ? h->cfg.bk : (nterms == 3 && c.cta_group == 1 ? 32 : 64);
+    switch (h->cfg.operand_layout) {
+        case GEMM_LAYOUT_K_MAJOR: c.kmajor = 1; break;
+        case GEMM_LAYOUT_AS_STORED: c.kmajor = 0; break;
+        default:
+            c.kmajor = call == Call::Split ? 1
+                       : call == Call::Bf16 ? (pack_pays(M, N, K, pack_a, pack_b) ? 1 : 0)
+                                            : 0;
+    }
     c.stages = h->cfg.stages;
     c.raster_group = h->cfg.raster_group ? h->cfg.raster_group : 16;
     c.max_ctas = h->cfg.max_ctas;
     c.poll_limit = h->cfg.wait_poll_limit;
     c.promote_k = h->cfg.promote_k == 0 ? 512 : (h->cfg.promote_k < 0 ? 0 : h->cfg.promote_k);
-    c.cta_group = h->cfg.cta_group == 0 ? 1 : h->cfg.cta_group;
-    // CTA pairs stage K-major tiles only
-    c.kmajor = (h->cfg.operand_layout == GEMM_LAYOUT_K_MAJOR || c.cta_group == 2) ? 1 : 0;
     if (h->cfg.split_k > 0) {
         c.split_k = h->cfg.split_k;
     } else {
@@ -253,8 +301,8 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     }
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
-    const TcLaunch cfg = plan_tc(h, nterms, M, N, K);
-    // op(A) is M x K and op(B)^T is N x K; each is split in its stored orientation
+    const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split);
+    // op(A) is M x K and op(B)^T is N x K, split K-major or as stored
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
     const WsPlan w = plan_ws(planes, pa.lay.plane, pb.lay.plane, M, N, K, cfg);
@@ -308,9 +356,7 @@ void handle_set_launches(gemm_handle_t h, int n) { h->last_launches = n; }
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
     // tile choice of the handle's configuration (problem-size independent
     // parts) for grouped launches, which use one CTA per 128-row tile
-    TcLaunch c = plan_tc(h, nterms, 1 << 20, 1 << 20, 1);
-    c.cta_group = 1;
-    c.kmajor = h->cfg.operand_layout == GEMM_LAYOUT_K_MAJOR ? 1 : 0;
+    TcLaunch c = plan_tc(h, nterms, 1 << 20, 1 << 20, 1, Call::Grouped);
     return c;
 }
 }  // namespace gb300
@@ -328,9 +374,8 @@ struct Syr2kPlan {
 
 Syr2kPlan plan_syr2k(const gemm_context* h, int nterms, int trans, int64_t N, int64_t K,
                      TcLaunch* cfg) {
-    *cfg = plan_tc(h, nterms, N, N, K);
+    *cfg = plan_tc(h, nterms, N, N, K, Call::Syr2k);
     cfg->split_k = 1;
-    cfg->cta_group = 1;
     Syr2kPlan sp;
     sp.planes = nterms == 3 ? 2 : 1;
     // an operand stored K x N (trans) stays MN-major unless K-major is asked for
@@ -400,7 +445,8 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         c.raster_group < 0 || c.max_ctas < 0 || c.promote_k < -1 || c.cta_group < 0 ||
         c.cta_group > 2 || (c.cta_group == 2 && c.bn == 128) ||
         c.wait_poll_limit < 0 ||
-        (c.operand_layout != GEMM_LAYOUT_AS_STORED && c.operand_layout != GEMM_LAYOUT_K_MAJOR) ||
+        (c.operand_layout != GEMM_LAYOUT_AUTO && c.operand_layout != GEMM_LAYOUT_K_MAJOR &&
+         c.operand_layout != GEMM_LAYOUT_AS_STORED) ||
         c.reserved != 0)
         return fail_arg(h, 2);
     h->cfg = c;
@@ -415,7 +461,7 @@ size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, 
     if ((transA != GEMM_OP_N && transA != GEMM_OP_T) || (transB != GEMM_OP_N && transB != GEMM_OP_T))
         return 0;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
-    const TcLaunch c = plan_tc(h, nterms, M, N, K);
+    const TcLaunch c = plan_tc(h, nterms, M, N, K, Call::Split);
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, c);
     // gemm() splits both operands; gemm_bf16 needs at most as much (packs only)
@@ -455,12 +501,12 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
         return status_of(gb300::launch_scale_c(M, N, beta, C, ldc, s));
     }
     if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
-    // Operands are read in place by TMA in their stored orientation: K-major
-    // (A stored M x K, B stored N x K) or MN-major (A stored K x M, B stored
-    // K x N).  Only when the launch wants every operand K-major are the
-    // MN-contiguous ones packed first.
-    const TcLaunch cfg = plan_tc(h, 1, M, N, K);
+    // K-contiguous operands (A stored M x K, B stored N x K) are read in place
+    // by TMA; MN-contiguous ones (A stored K x M, B stored K x N) are read in
+    // place as MN-major tiles, or packed K-contiguous first when the plan
+    // wants K-major operands.
     const bool a_kr = transA == GEMM_OP_T, b_kr = transB == GEMM_OP_N;  // stored K x rows
+    const TcLaunch cfg = plan_tc(h, 1, M, N, K, Call::Bf16, a_kr, b_kr);
     const bool pack_a = a_kr && cfg.kmajor;
     const bool pack_b = b_kr && cfg.kmajor;
     if (!pack_a && ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 8))) return GEMM_ERR_ALIGN;
@@ -573,7 +619,7 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     const bool tc = mode != GEMM_MODE_F32_SIMT;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
-    TcLaunch cfg = plan_tc(h, nterms, rb, N, K);
+    TcLaunch cfg = plan_tc(h, nterms, rb, N, K, Call::Split);
     cfg.split_k = 1;
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);

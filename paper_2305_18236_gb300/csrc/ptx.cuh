@@ -182,6 +182,34 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// 3-D tiled load into this CTA's shared memory whose transaction bytes are
+// counted on an mbarrier of the CTA pair's even CTA (`bar_cluster`: a
+// shared::cluster address from mapa_shared), the cta_group::2 form.
+__device__ __forceinline__ void tma_load_3d_to_peer_bar(void* smem_dst, const CUtensorMap* map,
+                                                        uint32_t bar_cluster, int32_t c0,
+                                                        int32_t c1, int32_t c2,
+                                                        uint64_t cache_hint) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar_cluster),
+        "l"(cache_hint)
+        : "memory");
+}
+
+// Account for `bytes` transaction bytes on a local mbarrier without a copy
+// (used to settle a phase whose partner copy was never issued).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 32-bit store to shared memory of another CTA of the cluster.
+__device__ __forceinline__ void st_shared_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
 // 3-D tiled load of the box at (c0, c1, c2) into shared memory; completion
 // is signalled on `bar` as transaction bytes.
 __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, uint64_t* bar,
@@ -380,19 +408,6 @@ __host__ __device__ constexpr uint64_t sdesc_fields(uint32_t lbo, uint32_t sbo, 
 // The descriptor of the tile at `smem_addr` (start address >> 4 in bits 0-13).
 __device__ __forceinline__ uint64_t sdesc_at(uint32_t smem_addr, uint64_t fields) {
     return fields | uint64_t((smem_addr & 0x3FFFF) >> 4);
-}
-
-// Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with a 128-byte (rows of 64 BF16) or 64-byte (rows of 32 BF16) swizzle.
-// Rows are `row_bytes` apart; 8-row swizzle atoms are 8 * row_bytes apart
-// (stride byte offset).  Bits: start >> 4 in 0-13, leading byte offset >> 4
-// in 16-29 (unused for swizzled K-major, set to 1), stride byte offset >> 4
-// in 32-45, version 1 in bits 46-47, layout in 61-63 (2 = 128B, 4 = 64B).
-__device__ __forceinline__ uint64_t make_sdesc_kmajor(uint32_t smem_addr, int row_bytes) {
-    const uint64_t layout = (row_bytes == 128) ? 2ull : 4ull;
-    const uint64_t sbo = uint64_t(8 * row_bytes) >> 4;
-    return uint64_t((smem_addr & 0x3FFFF) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) |
-           (layout << 61);
 }
 
 }  // namespace gb300

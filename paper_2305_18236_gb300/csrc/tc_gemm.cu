@@ -633,14 +633,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 // read both CTAs' tiles and write each CTA's 128 accumulator rows in its own
 // tensor memory.
 //
-// Synchronisation: each CTA's TMA signals its OWN full[s]; the odd CTA's
-// warp 1 forwards "my half of stage s landed" to the even CTA's peer_full[s]
-// with a remote arrive.  The even CTA's commits are multicast to both CTAs'
-// empty[s] / acc_full[b] / drain barriers; both CTAs' epilogue warps arrive on
-// the even CTA's acc_empty[b] (16 arrivals).  Keeping every TMA completion
-// local lets each producer drain its own copies on any exit path; a cluster
-// barrier before the tensor memory is freed keeps both CTAs alive until all
-// remote operations are done.
+// Synchronisation: both CTAs' TMA copies of stage s count their bytes on the
+// EVEN CTA's full[s] (the odd CTA uses the cta_group::2 form of the copy,
+// which may signal the pair's even CTA); the even producer arms each phase
+// for both halves (2 x STAGE bytes), so the MMA issuer's one wait covers the
+// whole 256-row stage.  (A design that signalled each CTA's own barrier and
+// forwarded the odd half with a remote mbarrier arrive ran at about one stage
+// per microsecond whatever the ring depth: the remote arrive on the critical
+// path of every stage, 2.6x slower.)  The even CTA's commits are multicast
+// to both CTAs' empty[s] / acc_full[b] / drain barriers; both CTAs' epilogue
+// warps arrive on the even CTA's acc_empty[b] (16 arrivals).
+//
+// Teardown: the odd producer cannot observe its own copies, so it reports how
+// many stages it filled (a remote store and arrive on odd_done); the even
+// producer settles every phase one producer armed or filled and the other did
+// not (complete_tx for a missing odd half, arrive.expect_tx for an odd half
+// the even side never armed), then waits for the last phase of every slot, so
+// all copies of both CTAs have landed before the cluster barrier that
+// precedes the tensor-memory free lets either CTA leave.
 template <int BN, int BK, int NTERMS>
 struct Shape2 {
     static constexpr int PLANES = NTERMS == 1 ? 1 : 2;
@@ -650,6 +660,7 @@ struct Shape2 {
     static constexpr int STAGE = PLANES * (A_PLANE + B_PLANE);
     static constexpr int TMEM_COLS = 2 * BN;
     static constexpr int ROW_BYTES = BK * 2;
+    static constexpr int MN_GROUP = PLANES * BK * 128;  // as in Shape
     static constexpr int BAR_BYTES = 1024;
     static constexpr int STAGING = kEpiWarps * 32 * 33 * 4;
     static_assert(B_PLANE % 1024 == 0, "B plane must keep swizzle atoms aligned");
@@ -659,6 +670,23 @@ struct Shape2 {
         return s > 8 ? 8 : s;
     }
 };
+
+// The pair form of load_operand: the even CTA's copies count on its own full
+// barrier, the odd CTA's on the even CTA's (`peer_bar`, cta_group::2 form).
+__device__ __forceinline__ void load_operand_pair(uint8_t* dst, const CUtensorMap* map,
+                                                  uint64_t* own_bar, uint32_t peer_bar, bool odd,
+                                                  int mn, int rows, int group_bytes, int kcoord,
+                                                  int row0, uint64_t pol) {
+    const int groups = mn ? rows / 64 : 1;
+    for (int g = 0; g < groups; ++g) {
+        const int x = mn ? row0 + g * 64 : kcoord;
+        const int y = mn ? kcoord : row0;
+        if (odd)
+            tma_load_3d_to_peer_bar(dst + g * group_bytes, map, peer_bar, x, y, 0, pol);
+        else
+            tma_load_3d(dst + g * group_bytes, map, own_bar, x, y, 0, pol);
+    }
+}
 
 template <int BN, int BK, int NTERMS, bool PROMOTE>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -671,14 +699,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                ~uintptr_t(1023));
     const int stages = p.stages;
     uint8_t* bar_area = smem + stages * S::STAGE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);
+    uint64_t* full = reinterpret_cast<uint64_t*>(bar_area);  // even CTA's count both halves
     uint64_t* empty = full + stages;
-    uint64_t* peer_full = empty + stages;
-    uint64_t* acc_full = peer_full + stages;  // [2]
-    uint64_t* acc_empty = acc_full + 2;       // [2]
+    uint64_t* acc_full = empty + stages;  // [2]
+    uint64_t* acc_empty = acc_full + 2;   // [2]
     uint64_t* drain = acc_empty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* odd_done = drain + 1;       // even CTA: the odd producer has finished
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(odd_done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile uint32_t* odd_fills = reinterpret_cast<volatile uint32_t*>(tmem_slot + 2);
     float* staging = reinterpret_cast<float*>(bar_area + S::BAR_BYTES);
 
     const int warp = threadIdx.x >> 5;
@@ -691,14 +720,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&peer_full[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
             mbar_init(&acc_empty[a], 2 * kEpiWarps);  // both CTAs' epilogue warps
         }
         mbar_init(drain, 1);
+        mbar_init(odd_done, 1);
         *abort_flag = 0;
+        *odd_fills = 0;
         fence_mbar_init();
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
@@ -718,8 +748,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------ TMA producer (both CTAs)
         if (lane == 0) {
             const uint64_t pol = l2_policy_evict_last();
-            uint32_t filled = 0, fill_par = 0;
-            int it = 0;
+            const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
+            int it = 0;  // stages this producer filled
             bool ok = true;
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
                 const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
@@ -731,27 +761,52 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t* st = smem + s * S::STAGE;
-                    mbar_arrive_expect_tx(&full[s], S::STAGE);
-                    tma_load_3d(st, &tmA, &full[s], kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, 0,
-                                pol);
-                    tma_load_3d(st + S::PLANES * S::A_PLANE, &tmB, &full[s], kb * BK,
-                                ti.nt * BN + int(rank) * S::BNH, 0, pol);
-                    filled |= 1u << s;
-                    fill_par = (fill_par & ~(1u << s)) | (ph << s);
+                    const uint32_t bar = leader_full + uint32_t(s) * 8u;
+                    if (rank == 0)
+                        mbar_arrive_expect_tx(&full[s], 2 * S::STAGE);  // both CTAs' halves
+                    load_operand_pair(st, &tmA, &full[s], bar, rank != 0, ti.maj & 1, kBM,
+                                      S::MN_GROUP, kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, pol);
+                    load_operand_pair(st + S::PLANES * S::A_PLANE, &tmB, &full[s], bar, rank != 0,
+                                      (ti.maj >> 1) & 1, S::BNH, S::MN_GROUP, kb * BK,
+                                      ti.nt * BN + int(rank) * S::BNH, pol);
                 }
             }
-            for (int s = 0; s < stages; ++s)
-                if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
+            if (rank != 0) {
+                // report the fill count to the even CTA (store, then release-arrive)
+                st_shared_cluster_u32(mapa_shared(smem_u32(const_cast<uint32_t*>(odd_fills)), 0),
+                                      uint32_t(it));
+                mbar_arrive_remote(mapa_shared(smem_u32(odd_done), 0));
+            } else {
+                // settle the phases only one producer reached, then wait until
+                // every copy of both CTAs has landed
+                int odd = it;
+                if (mbar_wait_drain_cluster(odd_done, 0, p.err)) odd = int(*odd_fills);
+                for (int j = min(it, odd); j < max(it, odd); ++j) {
+                    const int s = j % stages;
+                    if (j < it)
+                        mbar_complete_tx(&full[s], S::STAGE);  // odd half never issued
+                    else
+                        mbar_arrive_expect_tx(&full[s], S::STAGE);  // odd half only
+                }
+                const int last = max(it, odd);
+                for (int s = 0; s < stages && s < last; ++s) {
+                    const int j = last - 1 - ((last - 1 - s) % stages);  // last fill of slot s
+                    mbar_wait_drain(&full[s], uint32_t(j / stages) & 1, p.err);
+                }
+            }
         }
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {
             // -------------------------------------------- pair MMA issuer (even CTA)
-            constexpr uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN);
             int it = 0, g = 0;
             bool ok = true;
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
                 const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
+                const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
+                const uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN, a_mn, b_mn);
+                const OpLayout la = op_layout<S>(a_mn, S::A_PLANE);
+                const OpLayout lb = op_layout<S>(b_mn, S::B_PLANE);
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                     const int buf = g & 1;
@@ -767,35 +822,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int kb = c0; kb < c1; ++kb, ++it) {
                         const int s = it % stages;
                         const uint32_t ph = (it / stages) & 1;
-                        if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err) ||
-                            !mbar_wait_bounded_cluster(&peer_full[s], ph, p.lim, abort_flag,
-                                                       p.err)) {
-                            ok = false;
+                        if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
+                            ok = false;  // both CTAs' halves of stage s are counted on full[s]
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_hi = smem_u32(smem + s * S::STAGE);
-                        const uint32_t b_hi = a_hi + S::PLANES * S::A_PLANE;
+                        const uint32_t a_st = smem_u32(smem + s * S::STAGE);
+                        const uint32_t b_st = a_st + S::PLANES * S::A_PLANE;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t off = kk * 32;
+                            const uint32_t a_hi = a_st + kk * la.k_step;
+                            const uint32_t b_hi = b_st + kk * lb.k_step;
                             const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
                             if (NTERMS == 3) {
-                                const uint32_t a_lo = a_hi + S::A_PLANE;
-                                const uint32_t b_lo = b_hi + S::B_PLANE;
-                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_lo + off, S::ROW_BYTES),
-                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
-                                               acc);
-                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                               make_sdesc_kmajor(b_lo + off, S::ROW_BYTES), idesc,
-                                               1u);
-                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
-                                               1u);
+                                umma_bf16_pair(d_tmem, sdesc_at(a_hi + la.lo_off, la.fields),
+                                               sdesc_at(b_hi, lb.fields), idesc, acc);
+                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
+                                               sdesc_at(b_hi + lb.lo_off, lb.fields), idesc, 1u);
+                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
+                                               sdesc_at(b_hi, lb.fields), idesc, 1u);
                             } else {
-                                umma_bf16_pair(d_tmem, make_sdesc_kmajor(a_hi + off, S::ROW_BYTES),
-                                               make_sdesc_kmajor(b_hi + off, S::ROW_BYTES), idesc,
-                                               acc);
+                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
+                                               sdesc_at(b_hi, lb.fields), idesc, acc);
                             }
                         }
                         umma_commit_pair(&empty[s], 0x3);  // both CTAs may refill slot s
@@ -807,22 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit_pair(drain, 0x3);  // both CTAs learn when every pair MMA is done
             mbar_wait_drain_cluster(drain, 0, p.err);
         } else if (lane == 0) {
-            // -------------------------------------------- forwarder (odd CTA)
-            const uint32_t leader_peer_full = mapa_shared(smem_u32(peer_full), 0);
-            int it = 0;
-            bool ok = true;
-            for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
-                for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
-                    const int s = it % stages;
-                    const uint32_t ph = (it / stages) & 1;
-                    if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_remote(leader_peer_full + uint32_t(s) * 8u);
-                }
-            }
+            // -------------------------------------------- odd CTA
             // the even CTA's MMAs read this CTA's tiles and write its TMEM
             mbar_wait_drain_cluster(drain, 0, p.err);
         }
@@ -1110,7 +1143,6 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     const int bn = cfg.bn == 128 ? 128 : 256;
     const int bk = cfg.bk == 64 ? 64 : 32;
     const bool pair = cfg.cta_group == 2 && bn == 256;
-    if (pair && (a.mn_major || b.mn_major)) return -6;  // CTA pairs stage K-major tiles only
     const int bm = pair ? 2 * kBM : kBM;  // output rows per tile (per CTA pair)
     TcParams p{};
     p.maj = (a.mn_major ? 1 : 0) | (b.mn_major ? 2 : 0);

@@ -66,9 +66,10 @@ class Gemm:
 
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
-                   promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="as_stored"):
-        """operand_layout: "as_stored" (MN-major tiles for operands stored
-        K x rows) or "k_major" (every operand made K-contiguous first)."""
+                   promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="auto"):
+        """operand_layout: "auto" (library choice), "as_stored" (MN-major tiles
+        for operands stored K x rows) or "k_major" (every operand made
+        K-contiguous first)."""
         layout = LAYOUTS[operand_layout] if isinstance(operand_layout, str) else operand_layout
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
                             wait_poll_limit, layout, 0)
@@ -291,8 +292,10 @@ class GroupedPlan:
         ms = ctypes.c_double()
         check(self.lib.gemm_grouped_plan_config(self.plan, ctypes.byref(cfg), ctypes.byref(ms)),
               "gemm_grouped_plan_config")
+        names = {v: k for k, v in LAYOUTS.items()}
         return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
-                "raster_group": cfg.raster_group, "operand_layout": cfg.operand_layout,
+                "raster_group": cfg.raster_group,
+                "operand_layout": names.get(cfg.operand_layout, cfg.operand_layout),
                 "tuned_ms": ms.value}
 
     def close(self):

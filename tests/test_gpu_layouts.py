@@ -58,6 +58,21 @@ def test_as_stored_integer_bit_exact(mode, bn, bk, tA, tB):
 
 
 @pytest.mark.parametrize("tA,tB", TRANS)
+@pytest.mark.parametrize("bk", [32, 64])
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_cta_pair_as_stored_integer_bit_exact(mode, bk, tA, tB):
+    """The CTA-pair kernel with MN-major operands (each CTA stages 128 rows of
+    A and half of B as 64-row groups), ragged in every dimension, exact."""
+    h = _handle(cta_group=2, bn=256, bk=bk, operand_layout="as_stored")
+    M, N, K = 600, 530, 777
+    A, B, C0 = _integer_problem(M, N, K, tA, tB, 190 + bk)
+    C = run_mode(mode, A, B, 1.5, 0.5, C0, tA, tB, h=h)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
+    assert np.array_equal(C.astype(np.float64), ref)
+    h.close()
+
+
+@pytest.mark.parametrize("tA,tB", TRANS)
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 def test_k_major_integer_bit_exact(mode, tA, tB):
     h = _handle(operand_layout="k_major")
@@ -152,7 +167,7 @@ def test_grouped_layouts_integer_exact(layout):
                         C=torch.from_numpy(C0.copy()).cuda(), transA=tA, transB=tB, alpha=1.5,
                         beta=0.5))
     plan = g.GroupedPlan(dev, mode="bf16x3", h=h)
-    assert plan.config()["operand_layout"] == (0 if layout == "as_stored" else 1)
+    assert plan.config()["operand_layout"] == layout
     plan.run()
     torch.cuda.synchronize()
     for (A, B, C0, tA, tB), d in zip(probs, dev):
@@ -179,6 +194,33 @@ def test_from_host_transposed_a_blocks(layout):
     rows = np.linspace(0, M - 1, 48).astype(np.int64)
     C64, D, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=True, rows=rows)
     assert oracle.normwise_error(tC.numpy()[rows], C64, D) <= tol_exact("bf16x3", K)
+    h.close()
+
+
+def test_auto_layout_choice():
+    """Library choice: split operands K-major (workspace of K-major planes);
+    gemm_bf16 packs an MN-contiguous B only when the pass is cheap next to
+    the GEMM: a small NN problem reads B in place (one launch), a large one
+    packs it first (two launches)."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = _handle()
+    M, N, K = 1000, 3, 200
+
+    def r256(x):
+        return (x + 255) // 256 * 256
+
+    assert h.workspace_size("bf16x3", False, False, M, N, K) == \
+        r256(2 * M * K * 2) + r256(2 * N * K * 2)
+    for (m, n, k), launches in [((256, 512, 64), 1), ((4096, 4096, 4096), 2)]:
+        A = torch.ones((m, k), dtype=torch.bfloat16, device="cuda")
+        B = torch.ones((k, n), dtype=torch.bfloat16, device="cuda")
+        C = g.matmul_bf16(A, B, h=h)
+        torch.cuda.synchronize()
+        assert h.last_launch_count() == launches
+        assert bool((C == float(k)).all())
     h.close()
 
 
