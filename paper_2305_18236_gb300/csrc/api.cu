@@ -68,15 +68,18 @@ enum class Call {
     Syr2k,    // gemm_syr2k (one CTA per tile)
 };
 
-// True when packing the MN-contiguous BF16 operands K-contiguous costs less
-// than a tenth of the GEMM itself (time estimates at rough GB300 rates): the
-// K-major kernel is then faster overall; otherwise they are read in place.
+// True when packing the MN-contiguous BF16 operands K-contiguous (a launch
+// of about 5 us plus 4 bytes of traffic per element) costs less than a
+// tenth of the GEMM itself (time estimates at rough GB300 rates): the
+// K-major kernel, ~15 % faster on the tensor cores, then wins overall;
+// otherwise the operands are read in place.
 bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
     const double m = double(M), n = double(N), k = double(K);
     const double t_mma = 2.0 * m * n * k / 1.2e15;
     const double t_mem = (2.0 * (m * k + n * k) + 4.0 * m * n) / 6.0e12;
     const double packed = (pack_a ? m * k : 0.0) + (pack_b ? n * k : 0.0);
-    return 4.0 * packed / 6.0e12 < 0.1 * std::max(t_mma, t_mem);
+    if (packed == 0.0) return false;
+    return 5e-6 + 4.0 * packed / 6.0e12 < 0.1 * std::max(t_mma, t_mem);
 }
 
 // Tile plan of one tensor-core launch.  Library choice (configuration 0):

@@ -214,7 +214,7 @@ def test_auto_layout_choice():
 
     assert h.workspace_size("bf16x3", False, False, M, N, K) == \
         r256(2 * M * K * 2) + r256(2 * N * K * 2)
-    for (m, n, k), launches in [((256, 512, 64), 1), ((4096, 4096, 4096), 2)]:
+    for (m, n, k), launches in [((256, 512, 64), 1), ((8192, 8192, 8192), 2)]:
         A = torch.ones((m, k), dtype=torch.bfloat16, device="cuda")
         B = torch.ones((k, n), dtype=torch.bfloat16, device="cuda")
         C = g.matmul_bf16(A, B, h=h)
