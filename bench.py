@@ -52,10 +52,11 @@ def parse():
                         "without transposing and read as MN-major tiles; k_major: every operand "
                         "made K-contiguous first")
     p.add_argument("--workload", default="square",
-                   choices=["square", "rect", "grouped", "chain", "syr2k"],
+                   choices=["square", "rect", "grouped", "chain", "syr2k", "sweep"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
                         "grouped: 512 uneven problems; chain: Y = X W forward + backward; "
-                        "syr2k: the rank-2k update of Section 6.1 at N = K = --size")
+                        "syr2k: the rank-2k update of Section 6.1 at N = K = --size; "
+                        "sweep: sizes 1024..8192 x transposes x distributions x modes")
     return p.parse_args()
 
 
@@ -673,6 +674,88 @@ def run_syr2k(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """The square-size sweep: M = N = K in {1024, 2048, 4096, 8192} x {NN, NT,
+    TN, TT} x {U[-1, 1], sign-random 2^U[-10, 10]} x every mode, alpha 1.5,
+    beta 0.5, C0 U[-1, 1].  Each case is timed with CUDA events around each
+    call (L2 flushed with a 256 MB write between calls for sizes <= 2048);
+    its CPU baseline is the FP64 oracle on 8 sampled rows, which also gives
+    the case's normwise error."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    import oracle
+    from paper_2305_18236_gb300 import gemm as g
+    from paper_2305_18236_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    peaks, src = load_peaks()
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    flush = torch.empty(256 << 18, device="cuda")  # 256 MB
+    h = g.Gemm()
+    cases = []
+    for n in (1024, 2048, 4096, 8192):
+        for dist in ("uniform", "log_uniform"):
+            for tA, tB in ((False, False), (False, True), (True, False), (True, True)):
+                A = inputs.make(dist, (n, n), SEED + n, k=n)
+                B = inputs.make(dist, (n, n), SEED + n + 1, k=n)
+                C0 = inputs.uniform((n, n), SEED + n + 2)
+                rows = np.linspace(0, n - 1, 8).astype(np.int64)
+                t0 = time.perf_counter()
+                C64, D, used = oracle.gemm(A, B, ALPHA, BETA, C0, transA=tA, transB=tB, rows=rows)
+                cpu_s = time.perf_counter() - t0
+                dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+                dC0 = torch.from_numpy(C0).cuda()
+                for mode in ("f32_simt", "bf16", "bf16x3"):
+                    C = dC0.clone()
+                    g.matmul(dA, dB, C=C, alpha=ALPHA, beta=BETA, transA=tA, transB=tB,
+                             mode=mode, h=h)
+                    torch.cuda.synchronize()
+                    err = oracle.normwise_error(C.cpu().numpy()[rows], C64, D)
+                    steps = max(2, args.steps // (1 if n <= 4096 else 4)) if mode != "f32_simt" \
+                        else max(2, args.steps // (4 if n <= 4096 else 16))
+                    times = []
+                    for it in range(args.warmup + steps):
+                        if n <= 2048:
+                            flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        g.matmul(dA, dB, C=C, alpha=ALPHA, beta=BETA, transA=tA, transB=tB,
+                                 mode=mode, h=h)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        if it >= args.warmup:
+                            times.append(e0.elapsed_time(e1))
+                    ms = statistics.median(times)
+                    tflops = 2.0 * n ** 3 / ms / 1e9
+                    peak = fp32_peak if mode == "f32_simt" else bf16_peak / (3 if mode == "bf16x3" else 1)
+                    cases.append({"n": n, "trans": ("T" if tA else "N") + ("T" if tB else "N"),
+                                  "dist": dist, "mode": mode, "ms": round(ms, 5),
+                                  "tflops": round(tflops, 2), "pct_of_peak": round(100 * tflops / peak, 1),
+                                  "normwise_error": err,
+                                  "cpu_oracle_tflops": round(2.0 * len(rows) * n * n / cpu_s / 1e12, 5)})
+                    print(json.dumps(cases[-1]), file=sys.stderr, flush=True)
+                del dA, dB, dC0
+    h.close()
+    print(json.dumps({"metric": "square sweep: TFLOP/s and % of the mode's peak (FP32 SIMT: FP32 "
+                                "peak; BF16: BF16 peak; 3xBF16: BF16 peak / 3)",
+                      "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": "M=N=K in {1024..8192} x 4 transposes x 2 "
+                                             "distributions x 3 modes, alpha 1.5 beta 0.5",
+                                 "l2": "flushed between calls for n <= 2048"},
+                      "peaks": {"fp32_tflops": fp32_peak, "bf16_tflops": bf16_peak, "source": src},
+                      "cpu_baseline": {"kind": "oracle", "sample": "8 evenly spaced rows per case",
+                                       "cores": oracle.host_cores()},
+                      "cases": cases}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -685,6 +768,8 @@ def main():
         run_chain(args)
     elif args.workload == "syr2k":
         run_syr2k(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

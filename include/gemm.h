@@ -353,6 +353,11 @@ gemm_status_t gemm_sync(gemm_handle_t handle, void *stream);
  * (0 if the last call succeeded or failed for another reason). */
 int gemm_last_error_arg(gemm_handle_t handle);
 
+/* The same as a status-returning call (the BLAS xerbla convention): *pos
+ * receives the position; GEMM_ERR_ARG (position 1 or 2) for a NULL handle
+ * or pos. */
+gemm_status_t gemm_get_last_error_arg(gemm_handle_t handle, int *pos);
+
 /* Number of kernels the handle's last successful call enqueued. */
 int gemm_last_launch_count(gemm_handle_t handle);
 

@@ -82,6 +82,7 @@ _SIGS = {
                                            _vp, _i64, _vp, _i64, _f32, _vp, _i64, _vp]),
     "gemm_sync": (ctypes.c_int, [_vp, _vp]),
     "gemm_last_error_arg": (ctypes.c_int, [_vp]),
+    "gemm_get_last_error_arg": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "gemm_last_launch_count": (ctypes.c_int, [_vp]),
     "gemm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -880,6 +880,16 @@ gemm_status_t gemm_sync(gemm_handle_t h, void* stream) {
 
 int gemm_last_error_arg(gemm_handle_t h) { return h ? h->last_err_arg : 1; }
 
+gemm_status_t gemm_get_last_error_arg(gemm_handle_t h, int* pos) {
+    if (!h) {
+        if (pos) *pos = 1;
+        return GEMM_ERR_ARG;
+    }
+    if (!pos) return GEMM_ERR_ARG;  // the handle keeps its recorded position
+    *pos = h->last_err_arg;
+    return GEMM_OK;
+}
+
 int gemm_last_launch_count(gemm_handle_t h) { return h ? h->last_launches : 0; }
 
 const char* gemm_status_string(gemm_status_t s) {

@@ -34,9 +34,15 @@ __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
 }
 
 int grid_for(int64_t work, int per_block) {
+    static int sms_of[64] = {};  // SM count per device, queried once
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64 && sms_of[dev] > 0) {
+        sms = sms_of[dev];
+    } else {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (dev >= 0 && dev < 64) sms_of[dev] = sms;
+    }
     const int64_t want = (work + per_block - 1) / per_block;
     return int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 16)));
 }

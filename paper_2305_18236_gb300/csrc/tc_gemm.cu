@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -991,6 +992,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// Raise a kernel's dynamic shared-memory limit to the most any of its
+// launches asks for (kMaxSmem), once per kernel and device: the attribute
+// persists, and setting it on every call costs host time.  `done` is the
+// calling kernel's own bit set (bit d: device d).
+template <class Kernel>
+bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+        cudaSuccess)
+        return false;
+    done.fetch_or(bit, std::memory_order_release);
+    return true;
+}
+
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
                    TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
@@ -1003,8 +1021,8 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
     const int smem = std::max(S::smem_bytes(stages), min_smem);
     auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE, GROUPED>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -4;
+    static std::atomic<uint64_t> smem_set{0};  // bit d: limit raised on device d
+    if (!allow_max_smem(kern, smem_set)) return -4;
     int ctas = num_sms;
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
@@ -1023,8 +1041,8 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
     const int smem = std::max(S::smem_bytes(stages), min_smem);
     auto kern = tc_gemm_pair_kernel<BN, BK, NTERMS, PROMOTE>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-        return -4;
+    static std::atomic<uint64_t> smem_set{0};
+    if (!allow_max_smem(kern, smem_set)) return -4;
     int pairs = num_sms / 2;
     if (cfg.max_ctas > 0) pairs = std::min(pairs, std::max(1, cfg.max_ctas / 2));
     pairs = std::max(1, std::min(pairs, p.num_tiles));

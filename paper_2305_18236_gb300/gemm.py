@@ -52,6 +52,7 @@ class Gemm:
             check(self.lib.gemm_create(ctypes.byref(h)), "gemm_create")
         self.h = h
         self._ws = None
+        self._ws_sizes = {}  # (mode, transA, transB, M, N, K) -> bytes, for this config
 
     def close(self):
         if self.h:
@@ -74,20 +75,29 @@ class Gemm:
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
                             wait_poll_limit, layout, 0)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
+        self._ws_sizes.clear()
 
     def reset_config(self):
         check(self.lib.gemm_set_config(self.h, None), "gemm_set_config", self.h)
+        self._ws_sizes.clear()
 
     def ensure_workspace(self, nbytes):
         if nbytes == 0:
             return
         if self._ws is None or self._ws.numel() < nbytes:
             self._ws = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
-        check(self.lib.gemm_set_workspace(self.h, ctypes.c_void_p(self._ws.data_ptr()),
-                                          self._ws.numel()), "gemm_set_workspace", self.h)
+            check(self.lib.gemm_set_workspace(self.h, ctypes.c_void_p(self._ws.data_ptr()),
+                                              self._ws.numel()), "gemm_set_workspace", self.h)
 
     def workspace_size(self, mode, transA, transB, M, N, K):
-        return self.lib.gemm_workspace_size(self.h, _mode(mode), int(transA), int(transB), M, N, K)
+        key = (_mode(mode), bool(transA), bool(transB), M, N, K)
+        n = self._ws_sizes.get(key)
+        if n is None:
+            n = self.lib.gemm_workspace_size(self.h, key[0], int(transA), int(transB), M, N, K)
+            if len(self._ws_sizes) > 4096:
+                self._ws_sizes.clear()
+            self._ws_sizes[key] = n
+        return n
 
     def last_launch_count(self):
         return self.lib.gemm_last_launch_count(self.h)

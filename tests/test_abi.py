@@ -61,6 +61,9 @@ def test_null_handle_is_argument_one(lib):
     assert lib.gemm_syr2k(None, 0, 0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 0, None) \
         == _lib.GEMM_ERR_ARG
     assert lib.gemm_syr2k_workspace_size(None, 2, 0, 4, 4) == 0
+    pos = ctypes.c_int(0)
+    assert lib.gemm_get_last_error_arg(None, ctypes.byref(pos)) == _lib.GEMM_ERR_ARG
+    assert pos.value == 1
     assert lib.gemm_destroy(None) == _lib.GEMM_OK
     assert lib.gemm_last_error_arg(None) == 1
 
