@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2305_18236_gb300 import inputs
-from tests.gpu_util import MODES, check_mode, make_problem, run_mode, tol_terms
+from tests.gpu_util import MODES, check_mode, make_problem, run_mode, tol_exact, tol_terms
 
 pytestmark = pytest.mark.gpu
 TRANS = [(False, False), (False, True), (True, False), (True, True)]
@@ -235,22 +235,30 @@ def test_cta_pair_kernel(mode, bk, split):
     h.close()
 
 
-def test_cta_pair_timeout_path():
-    """The pair kernel's bounded waits expire cleanly too (one-poll limit)."""
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("layout", ["k_major", "as_stored"])
+def test_cta_pair_timeout_path(layout, mode):
+    """The pair kernel's bounded waits expire cleanly too (one-poll limit):
+    the even producer settles the stages each CTA filled, every copy lands
+    before either CTA leaves, and the next call on the context is correct."""
     import torch
 
     from paper_2305_18236_gb300 import _lib
     from paper_2305_18236_gb300 import gemm as g
 
     h = g.Gemm()
-    h.set_config(bn=256, cta_group=2, wait_poll_limit=1)
+    h.set_config(bn=256, cta_group=2, wait_poll_limit=1, operand_layout=layout)
     A, B, _ = make_problem(1024, 1024, 2048, seed=85)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     C = torch.zeros((1024, 1024), device="cuda")
-    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, mode="bf16x3", h=h)
+    g.matmul(dA, dB, C=C, mode=mode, h=h)
     assert h.sync() == _lib.GEMM_ERR_TIMEOUT
-    h.reset_config()
-    g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C=C, mode="bf16x3", h=h)
+    h.set_config(bn=256, cta_group=2, operand_layout=layout)
+    g.matmul(dA, dB, C=C, mode=mode, h=h)
     assert h.sync() == _lib.GEMM_OK
+    rows = np.arange(0, 1024, 101)
+    C64, D, _ = oracle.gemm(A, B, rows=rows)
+    assert oracle.normwise_error(C.cpu().numpy()[rows], C64, D) <= tol_exact(mode, 2048)
     h.close()
 
 

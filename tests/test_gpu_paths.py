@@ -166,6 +166,9 @@ def test_argument_errors_report_position():
         st = lib.gemm(*args)
         assert st == _lib.GEMM_ERR_ARG, pos
         assert lib.gemm_last_error_arg(h.h) == pos
+        got = ctypes.c_int(0)
+        assert lib.gemm_get_last_error_arg(h.h, ctypes.byref(got)) == _lib.GEMM_OK
+        assert got.value == pos
     # transposed storage changes which ld bound applies
     args = list(base)
     args[1], args[3], args[8] = 1, 20, 8  # A stored K x M = 8 x 20 needs lda >= 20
@@ -184,7 +187,7 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
     from paper_2305_18236_gb300 import gemm as g
 
     h = g.Gemm()
-    h.set_config(wait_poll_limit=1)
+    h.set_config(wait_poll_limit=1, cta_group=1)
     A, B, _ = make_problem(1024, 1024, 4096, seed=111)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     C = torch.zeros((1024, 1024), device="cuda")
