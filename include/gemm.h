@@ -171,7 +171,8 @@ gemm_status_t gemm(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
  * MN-contiguous ones (A stored K x M, B stored K x N) are either read in
  * place as MN-major tiles (same alignment rule) or first packed K-contiguous
  * into workspace (Algorithm 1's pack step; any ld), as operand_layout says
- * (library choice: packed when the pass costs under a tenth of the GEMM).  Argument positions as for gemm() (no mode; 15 is stream). */
+ * (library choice: packed when the pass costs under a tenth of the GEMM or
+ * when the operand cannot be read in place).  Argument positions as for gemm() (no mode; 15 is stream). */
 gemm_status_t gemm_bf16(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                         int64_t M, int64_t N, int64_t K,
                         float alpha, const uint16_t *A, int64_t lda,

@@ -510,10 +510,16 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
     // wants K-major operands.
     const bool a_kr = transA == GEMM_OP_T, b_kr = transB == GEMM_OP_N;  // stored K x rows
     const TcLaunch cfg = plan_tc(h, 1, M, N, K, Call::Bf16, a_kr, b_kr);
-    const bool pack_a = a_kr && cfg.kmajor;
-    const bool pack_b = b_kr && cfg.kmajor;
-    if (!pack_a && ((reinterpret_cast<uintptr_t>(A) & 15) || (lda % 8))) return GEMM_ERR_ALIGN;
-    if (!pack_b && ((reinterpret_cast<uintptr_t>(B) & 15) || (ldb % 8))) return GEMM_ERR_ALIGN;
+    auto misaligned = [](const void* p, int64_t ld) {
+        return (reinterpret_cast<uintptr_t>(p) & 15) != 0 || ld % 8 != 0;
+    };
+    // With the library's layout choice an MN-contiguous operand that TMA
+    // cannot read in place is packed instead of rejected.
+    const bool lib_choice = h->cfg.operand_layout == GEMM_LAYOUT_AUTO;
+    const bool pack_a = a_kr && (cfg.kmajor || (lib_choice && misaligned(A, lda)));
+    const bool pack_b = b_kr && (cfg.kmajor || (lib_choice && misaligned(B, ldb)));
+    if (!pack_a && misaligned(A, lda)) return GEMM_ERR_ALIGN;
+    if (!pack_b && misaligned(B, ldb)) return GEMM_ERR_ALIGN;
     const gb300::PackedLayout la = gb300::packed_layout(M, K, false);
     const gb300::PackedLayout lb = gb300::packed_layout(N, K, false);
     const WsPlan w = plan_ws(1, pack_a ? la.plane : 0, pack_b ? lb.plane : 0, M, N, K, cfg);

@@ -115,9 +115,10 @@ def test_as_stored_split_k_exact(tA, tB, split):
 
 
 def test_bf16_in_place_mn_major_alignment():
-    """gemm_bf16 reads a K x N B in place (MN-major): ldb % 8 != 0 is
-    GEMM_ERR_ALIGN; with the K-major layout the same call packs B first and
-    succeeds with the oracle's answer."""
+    """gemm_bf16 reads a K x N B in place (MN-major): with the stored layout
+    forced, ldb % 8 != 0 is GEMM_ERR_ALIGN; with the K-major layout, or the
+    library's choice, the same call packs B first and succeeds with the
+    oracle's answer."""
     import torch
 
     from paper_2305_18236_gb300 import _lib
@@ -140,11 +141,13 @@ def test_bf16_in_place_mn_major_alignment():
         g.matmul_bf16(A, Bt, h=h)
     assert e.value.status == _lib.GEMM_ERR_ALIGN
     h.close()
-    h = _handle(operand_layout="k_major")
-    C = g.matmul_bf16(A, Bt, h=h)
-    torch.cuda.synchronize()
-    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
-    h.close()
+    for layout in ("k_major", "auto"):
+        h = _handle(operand_layout=layout)
+        C = g.matmul_bf16(A, Bt, h=h)
+        torch.cuda.synchronize()
+        assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+        assert h.last_launch_count() == 2  # pack + GEMM
+        h.close()
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
