@@ -171,14 +171,22 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest of the ranks' values (the slowest replica's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_tflops(flops_per_step, steps, ms_max, world):
+    """Whole-job throughput of `world` independent replicas: every rank did
+    `steps` steps of `flops_per_step` in at most `ms_max` milliseconds."""
+    return world * flops_per_step * steps / (ms_max / 1e3) / 1e12
 
 
 def square_config(n, mode, world, layout=None):
@@ -340,7 +348,7 @@ def run_ours(args):
         raise RuntimeError("kernel reported a bounded-wait timeout")
     ms_max = max_over_ranks(ms, world)
     flops = 2.0 * M * N * K
-    value = world * flops * args.steps / (ms_max / 1e3) / 1e12
+    value = replica_tflops(flops, args.steps, ms_max, world)
     kernel_ms = main_ms.value / max(1, main_n.value)
 
     peaks, peak_src = load_peaks()
