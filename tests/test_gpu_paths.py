@@ -176,6 +176,26 @@ def test_argument_errors_report_position():
     h.close()
 
 
+def test_sizes_beyond_the_index_range_are_unsupported():
+    """M, N or K of 2**31 or more (beyond the kernels' 32-bit tile indices) is
+    GEMM_ERR_UNSUPPORTED before anything is launched; K = 0 and M = 0 are
+    quick returns (nothing read)."""
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    lib = h.lib
+    p = ctypes.c_void_p(16)  # never dereferenced
+    big = 1 << 31
+    for M, N, K, lda, ldb in [(big, 8, 8, 8, 8), (8, big, 8, 8, big), (8, 8, big, big, 8)]:
+        for mode in (0, 1, 2):
+            st = lib.gemm(h.h, 0, 0, M, N, K, 1.0, p, lda, p, ldb, 0.0, p, N, mode, None)
+            assert st == _lib.GEMM_ERR_UNSUPPORTED, (M, N, K, mode)
+    assert lib.gemm(h.h, 0, 0, 0, 8, 8, 1.0, None, 8, None, 8, 0.0, None, 8, 2, None) == _lib.GEMM_OK
+    assert h.last_launch_count() == 0
+    h.close()
+
+
 def test_bounded_wait_timeout_is_reported_and_context_survives():
     """A poll limit of one makes the tensor-core kernel's first wait on data
     still in flight expire: the kernel drains its own copies, frees tensor
