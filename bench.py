@@ -547,15 +547,19 @@ def run_grouped(args):
     h.set_config(operand_layout=args.operand_layout)
     res = {}
     with torch.cuda.stream(stream):
-        for name, kw in [("fixed_eager", dict()), ("fixed_graph", dict(graph=True)),
-                         ("tuned_graph", dict(autotune=True, graph=True))]:
+        hp = g.Gemm()
+        hp.set_config(operand_layout=args.operand_layout, cta_group=1)
+        for name, kw, hh in [("model_eager", dict(), h), ("model_graph", dict(graph=True), h),
+                             ("one_cta_graph", dict(graph=True), hp),
+                             ("tuned_graph", dict(autotune=True, graph=True), h)]:
             t0 = time.perf_counter()
-            plan = g.GroupedPlan(probs, mode=args.mode, h=h, **kw)
+            plan = g.GroupedPlan(probs, mode=args.mode, h=hh, **kw)
             create_s = time.perf_counter() - t0
             ms = _events_ms(plan.run, args.steps, args.warmup, stream)
             res[name] = {"ms": ms, "tflops": flops / ms / 1e9, "config": plan.config(),
                          "plan_create_s": create_s}
             plan.close()
+        hp.close()
     best = res["tuned_graph"]
     print(json.dumps({"metric": "grouped GEMM TFLOP/s, 512 problems (2MNK summed)",
                       "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1,

@@ -87,9 +87,13 @@ typedef struct gemm_context *gemm_handle_t;
  *    SMs shares a 256-row tile, each staging half of B; bn must be 256);
  *    0 = library choice: pairs for GEMM_MODE_BF16X3 in gemm(),
  *    gemm_from_host and gemm_backward when the problem has at least as many
- *    256 x 256 tiles as the GPU has SM pairs, else one CTA per tile (grouped
- *    launches and gemm_syr2k always use one CTA per tile).  bk 0 = 64, or
- *    32 for GEMM_MODE_BF16X3 with one CTA per tile.
+ *    256 x 256 tiles as the GPU has SM pairs, else one CTA per tile;
+ *    gemm_syr2k always uses one CTA per tile; grouped plans and
+ *    gemm_grouped on a handle that sets none of bn, bk, stages and
+ *    cta_group take the tile shape, depth and grouping that an analytic cost
+ *    model (padded tensor work, wave quantisation, measured per-clock
+ *    efficiency) ranks first.  bk 0 = 64, or 32 for GEMM_MODE_BF16X3 with
+ *    one CTA per tile.
  *  wait_poll_limit: mbarrier polls before a kernel abandons a wait, sets
  *    the device error word and exits cleanly (0 = default, about seconds).
  *  operand_layout: GEMM_LAYOUT_K_MAJOR (1): every operand is made
@@ -249,7 +253,9 @@ enum {
  * the fastest is kept; results are cached per process (and in the
  * file named by the GEMM_AUTOTUNE_CACHE environment variable, if set) keyed
  * by SM count, mode and problem shapes.  Tuning runs on `stream` and
- * synchronises it.  Without it, the handle's configuration is used.  The
+ * synchronises it.  Without it, a handle that sets none of bn, bk, stages
+ * and cta_group gets the cost model's first choice, untimed; otherwise the
+ * handle's configuration is used.  The
  * problems' pointers and sizes are fixed at creation.  Positions: 1 handle,
  * 2 mode, 3 host_problems (100 + i for problem i), 4 count, 5 flags,
  * 6 stream, 7 plan. */

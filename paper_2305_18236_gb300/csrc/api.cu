@@ -97,9 +97,8 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
                  bool pack_a = false, bool pack_b = false) {
     TcLaunch c;
     c.bn = h->cfg.bn ? h->cfg.bn : 256;
-    const bool one_cta_only = call == Call::Grouped || call == Call::Syr2k;
-    if (one_cta_only) {
-        c.cta_group = 1;
+    if (call == Call::Syr2k) {
+        c.cta_group = 1;  // the triangle walk exists in the one-CTA kernel only
     } else if (h->cfg.cta_group != 0) {
         c.cta_group = h->cfg.cta_group;
     } else {
@@ -356,9 +355,13 @@ int handle_num_sms(gemm_handle_t h) { return h->num_sms; }
 int* handle_err_word(gemm_handle_t h) { return h->err_word; }
 void handle_set_err_arg(gemm_handle_t h, int pos) { h->last_err_arg = pos; }
 void handle_set_launches(gemm_handle_t h, int n) { h->last_launches = n; }
+bool handle_tile_auto(gemm_handle_t h) {
+    // no tile shape, ring depth or CTA grouping forced by the handle
+    return h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.stages == 0 && h->cfg.cta_group == 0;
+}
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
     // tile choice of the handle's configuration (problem-size independent
-    // parts) for grouped launches, which use one CTA per 128-row tile
+    // parts) for grouped launches
     TcLaunch c = plan_tc(h, nterms, 1 << 20, 1 << 20, 1, Call::Grouped);
     return c;
 }

@@ -77,9 +77,13 @@ struct HostProb {
 };
 
 // Problem table and tensor maps for a tile shape; returns total tiles.
-int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
+// Tiles are 128 x bn (one CTA) or 256 x bn (CTA pairs, each CTA staging
+// bn / 2 rows of B).
+int build_tables(const std::vector<HostProb>& ps, const TcLaunch& cfg,
                  std::vector<GroupedProblem>& probs, std::vector<CUtensorMap>& maps,
                  std::vector<int>& tile_prob, bool* ok) {
+    const int bn = cfg.bn, bk = cfg.bk;
+    const int cg = cfg.cta_group == 2 ? 2 : 1;
     probs.clear();
     tile_prob.clear();
     maps.assign(2 * ps.size(), CUtensorMap{});
@@ -93,7 +97,7 @@ int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
         g.M = int(q.M);
         g.N = int(q.N);
         g.K = int(q.K);
-        g.num_m = int((q.M + 127) / 128);
+        g.num_m = int((q.M + 128 * cg - 1) / (128 * cg));
         g.num_n = int((q.N + bn - 1) / bn);
         g.k_blocks = int((q.K + bk - 1) / bk);
         g.tile_start = tiles;
@@ -104,17 +108,28 @@ int build_tables(const std::vector<HostProb>& ps, int bn, int bk, int nterms,
         tile_prob.insert(tile_prob.end(), size_t(g.num_m) * g.num_n, int(i));
         probs.push_back(g);
         if (!gb300::encode_operand(&maps[2 * i], q.a, bk, 128) ||
-            !gb300::encode_operand(&maps[2 * i + 1], q.b, bk, bn))
+            !gb300::encode_operand(&maps[2 * i + 1], q.b, bk, bn / cg))
             *ok = false;
     }
-    (void)nterms;
     return tiles;
 }
 
-// Analytic seed: which (BN, BK) exist on this SM and what they should cost.
-// Cost = padded tensor work of every tile (tiles are 128 x BN, so ragged
-// edges waste work) times the wave-quantisation factor of the persistent
-// grid, times a penalty for rings shallower than four stages.
+// Analytic seed: which (BN, BK, one CTA or CTA pairs) exist on this SM and
+// what they should cost.  Cost = padded tensor work of every tile (tiles are
+// 128 x BN or, for pairs, 256 x BN, and K is padded to BK, so ragged edges
+// waste work) times the wave-quantisation factor of the persistent grid,
+// divided by the configuration's efficiency: its padded work per second,
+// measured on 512 uneven problems (M, N, K in 32 * U{2..64}, 3xBF16) with the
+// split pass subtracted, relative to the fastest.  Pairs with BK 64 ran at
+// the sustained tensor rate; smaller stages pay a per-stage cost that no
+// padding term shows (pairs with BK 32 at 0.83, one CTA with BN 128 and
+// BK 32 at 0.58), and one CTA is bounded by the SM's operand intake (0.86).
+double config_efficiency(int cg, int bn, int bk) {
+    if (cg == 2) return bk == 64 ? 1.00 : 0.83;
+    if (bn == 256) return bk == 32 ? 0.86 : 0.83;
+    return bk == 64 ? 0.73 : 0.58;
+}
+
 struct Candidate {
     TcLaunch cfg;
     double model;
@@ -124,34 +139,37 @@ std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nter
                                        const TcLaunch& base) {
     std::vector<Candidate> out;
     const int kmax_smem = 232448;
-    for (int bn : {256, 128}) {
-        for (int bk : {32, 64}) {
-            int stages = 0;
-            for (int s = 8; s >= 2; --s)
-                if (gb300::tc_smem_bytes(nterms, bn, bk, s) <= kmax_smem) {
-                    stages = s;
-                    break;
+    for (int cg : {1, 2}) {
+        for (int bn : {256, 128}) {
+            for (int bk : {32, 64}) {
+                if (cg == 2 && (bn != 256 || nterms != 3)) continue;  // pair kernels compiled
+                int stages = 0;
+                for (int s = 8; s >= 2; --s)
+                    if (gb300::tc_smem_bytes(nterms, bn, bk, s, cg) <= kmax_smem) {
+                        stages = s;
+                        break;
+                    }
+                if (stages < 2 || 2 * bn > 512) continue;  // shared memory or TMEM does not fit
+                const int bm = 128 * cg;
+                double work = 0.0, tiles = 0.0;
+                for (const HostProb& q : ps) {
+                    const double nm = double((q.M + bm - 1) / bm), nn = double((q.N + bn - 1) / bn);
+                    const double kk = double((q.K + bk - 1) / bk) * bk;
+                    work += nm * nn * double(bm) * bn * kk;
+                    tiles += nm * nn;
                 }
-            if (stages < 2 || 2 * bn > 512) continue;  // shared memory or TMEM does not fit
-            double work = 0.0, tiles = 0.0;
-            for (const HostProb& q : ps) {
-                const double nm = double((q.M + 127) / 128), nn = double((q.N + bn - 1) / bn);
-                const double kk = double((q.K + bk - 1) / bk) * bk;
-                work += nm * nn * 128.0 * bn * kk;
-                tiles += nm * nn;
+                const double units = double(num_sms / cg);  // CTAs or CTA pairs
+                const double waves = std::ceil(tiles / units) / (tiles / units);
+                Candidate c;
+                c.cfg = base;
+                c.cfg.bn = bn;
+                c.cfg.bk = bk;
+                c.cfg.stages = stages;
+                c.cfg.split_k = 1;
+                c.cfg.cta_group = cg;
+                c.model = work * waves / config_efficiency(cg, bn, bk);
+                out.push_back(c);
             }
-            const double waves = std::ceil(tiles / num_sms) / (tiles / num_sms);
-            const double shallow = stages < 4 ? 1.15 : 1.0;
-            // 128 x 128 tiles read A twice per output element: extra operand traffic
-            const double narrow = bn == 128 ? 1.10 : 1.0;
-            Candidate c;
-            c.cfg = base;
-            c.cfg.bn = bn;
-            c.cfg.bk = bk;
-            c.cfg.stages = stages;
-            c.cfg.split_k = 1;
-            c.model = work * waves * shallow * narrow;
-            out.push_back(c);
         }
     }
     std::sort(out.begin(), out.end(),
@@ -187,22 +205,24 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
         *out = it->second;
         return true;
     }
-    // optional persistent cache: lines "key bn bk stages raster"
+    // optional persistent cache: lines "key bn bk stages raster cta_group"
+    // (lines without the last field are one-CTA configurations)
     const char* path = getenv("GEMM_AUTOTUNE_CACHE");
     if (!path) return false;
     FILE* f = fopen(path, "r");
     if (!f) return false;
-    char k[128];
-    int bn, bk, st, rg;
+    char line[256], k[128];
     bool found = false;
-    while (fscanf(f, "%127s %d %d %d %d", k, &bn, &bk, &st, &rg) == 5) {
-        if (key == k) {
-            out->bn = bn;
-            out->bk = bk;
-            out->stages = st;
-            out->raster_group = rg;
-            found = true;
-        }
+    while (fgets(line, sizeof line, f)) {
+        int bn, bk, st, rg, cg = 1;
+        const int n = sscanf(line, "%127s %d %d %d %d %d", k, &bn, &bk, &st, &rg, &cg);
+        if (n < 5 || key != k) continue;
+        out->bn = bn;
+        out->bk = bk;
+        out->stages = st;
+        out->raster_group = rg;
+        out->cta_group = cg == 2 ? 2 : 1;
+        found = true;
     }
     fclose(f);
     if (found) g_cache[key] = *out;
@@ -216,7 +236,8 @@ void cache_store(const std::string& key, const TcLaunch& c) {
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group);
+    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
+            c.cta_group);
     fclose(f);
 }
 
@@ -253,7 +274,7 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
     bool ok = true;
-    const int tiles = build_tables(sub, cfg.bn, cfg.bk, nterms, probs, maps, tile_prob, &ok);
+    const int tiles = build_tables(sub, cfg, probs, maps, tile_prob, &ok);
     if (!ok) return -1.0;
     GroupedProblem* dp = nullptr;
     CUtensorMap* dm = nullptr;
@@ -311,6 +332,7 @@ int* handle_err_word(gemm_handle_t h);
 void handle_set_err_arg(gemm_handle_t h, int pos);
 void handle_set_launches(gemm_handle_t h, int n);
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms);
+bool handle_tile_auto(gemm_handle_t h);
 }  // namespace gb300
 
 extern "C" {
@@ -357,7 +379,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     p->flags = flags;
     p->cfg = gb300::handle_tc_config(h, nterms);
     p->cfg.split_k = 1;
-    p->cfg.cta_group = 1;  // grouped launches use one CTA per 128-row tile
+    // grouped CTA-pair kernels exist for the split-precision mode with bn 256
+    if (p->cfg.cta_group == 2 && (nterms != 3 || p->cfg.bn != 256)) p->cfg.cta_group = 1;
 
     // Workspace layout: per problem, the hi (and lo) planes of A, then of B.
     // An operand stored K x rows (A with transA, B without transB) keeps that
@@ -447,6 +470,11 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         return st;
     }
 
+    if (!(flags & GEMM_GROUPED_AUTOTUNE) && !ps.empty() && gb300::handle_tile_auto(h)) {
+        // library choice without timing: the analytic model's best configuration
+        const std::vector<Candidate> cands = seed_candidates(ps, nterms, p->num_sms, p->cfg);
+        if (!cands.empty()) p->cfg = cands.front().cfg;
+    }
     if ((flags & GEMM_GROUPED_AUTOTUNE) && !ps.empty()) {
         const std::string key = shape_key(p->num_sms, nterms, ps);
         TcLaunch hit = p->cfg;
@@ -455,6 +483,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->cfg.bk = hit.bk;
             p->cfg.stages = hit.stages;
             p->cfg.raster_group = hit.raster_group;
+            p->cfg.cta_group = hit.cta_group;
         } else {
             // operands must be split before the candidates can be timed
             if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
@@ -526,7 +555,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
     bool ok = true;
-    p->total_tiles = build_tables(ps, p->cfg.bn, p->cfg.bk, nterms, probs, maps, tile_prob, &ok);
+    p->total_tiles = build_tables(ps, p->cfg, probs, maps, tile_prob, &ok);
     if (!ok) {
         free_plan(p);
         return GEMM_ERR_CUDA;
@@ -582,7 +611,7 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg
         cfg->raster_group = p->cfg.raster_group;
         cfg->max_ctas = p->cfg.max_ctas;
         cfg->promote_k = p->cfg.promote_k > 0 ? p->cfg.promote_k : -1;
-        cfg->cta_group = 1;
+        cfg->cta_group = p->cfg.cta_group;
         cfg->wait_poll_limit = p->cfg.poll_limit;
         cfg->operand_layout = p->cfg.kmajor ? GEMM_LAYOUT_K_MAJOR : GEMM_LAYOUT_AS_STORED;
         cfg->reserved = 0;

@@ -72,15 +72,18 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
 
 // Grouped launch: `count` problems described by dev_problems (device) with
 // two tensor maps each in dev_maps (device, encoded with cfg.bk and a box of
-// 128 rows for A and cfg.bn rows for B); total_tiles = sum of num_m * num_n;
-// dev_tile_prob[t] = index of the problem that owns tile t.
+// 128 rows for A and cfg.bn / cfg.cta_group rows for B); total_tiles = sum of
+// num_m * num_n, with num_m counting tiles of 128 * cfg.cta_group rows;
+// dev_tile_prob[t] = index of the problem that owns tile t.  cta_group 2
+// runs the CTA-pair kernel (split precision, bn 256 only).
 int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev_problems,
                       const CUtensorMap* dev_maps, const int* dev_tile_prob, int count,
                       int total_tiles, int* err_word, int num_sms, cudaStream_t stream);
 
-// Dynamic shared memory the tensor-core kernel asks for with this config
-// (0 if the configuration does not exist).
-int tc_smem_bytes(int nterms, int bn, int bk, int stages);
+// Dynamic shared memory the tensor-core kernel (one CTA per tile, or CTA
+// pairs with cta_group 2) asks for with this config (0 if the configuration
+// does not exist).
+int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group = 1);
 
 // C <- alpha * A_op B_op^T + beta * C where A_op is M x K and B_op is N x K
 // (both K-contiguous BF16); nterms = 1 (hi.hi) or 3 (lo.hi + hi.lo + hi.hi).

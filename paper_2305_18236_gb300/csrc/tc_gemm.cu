@@ -689,7 +689,7 @@ __device__ __forceinline__ void load_operand_pair(uint8_t* dst, const CUtensorMa
     }
 }
 
-template <int BN, int BK, int NTERMS, bool PROMOTE>
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
@@ -731,8 +731,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         *odd_fills = 0;
         fence_mbar_init();
-        tma_prefetch_desc(&tmA);
-        tma_prefetch_desc(&tmB);
+        if (!GROUPED) {
+            tma_prefetch_desc(&tmA);
+            tma_prefetch_desc(&tmB);
+        }
     }
     __syncthreads();
     cluster_sync();  // barriers initialised in both CTAs before any remote arrive
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0;  // stages this producer filled
             bool ok = true;
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
                     const int s = it % stages;
                     const uint32_t ph = (it / stages) & 1;
@@ -765,9 +767,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t bar = leader_full + uint32_t(s) * 8u;
                     if (rank == 0)
                         mbar_arrive_expect_tx(&full[s], 2 * S::STAGE);  // both CTAs' halves
-                    load_operand_pair(st, &tmA, &full[s], bar, rank != 0, ti.maj & 1, kBM,
+                    load_operand_pair(st, ti.ma, &full[s], bar, rank != 0, ti.maj & 1, kBM,
                                       S::MN_GROUP, kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, pol);
-                    load_operand_pair(st + S::PLANES * S::A_PLANE, &tmB, &full[s], bar, rank != 0,
+                    load_operand_pair(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], bar, rank != 0,
                                       (ti.maj >> 1) & 1, S::BNH, S::MN_GROUP, kb * BK,
                                       ti.nt * BN + int(rank) * S::BNH, pol);
                 }
@@ -802,7 +804,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0, g = 0;
             bool ok = true;
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-                const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
                 const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
                 const uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN, a_mn, b_mn);
@@ -874,7 +876,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
 #pragma unroll 1
         for (int t = pair; t < p.num_tiles && ok; t += npairs) {
-            const TileInfo ti = get_tile<false>(t, p, &tmA, &tmB);
+            const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
             const int kb0 = ti.kb0, kb1 = ti.kb1;
             const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
             const int row0 = ti.mt * 2 * kBM + int(rank) * kBM + ew * 32;
@@ -895,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
                 if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1)
-                    prefetch_c(get_epi<false>(0, ti.ks, p), row0, col0, COLS, lane);
+                    prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0, col0, COLS, lane);
                 if (PROMOTE) {
                     if (c0 == kb0) {
 #pragma unroll
@@ -925,7 +927,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive_remote(leader_acc_empty + uint32_t(buf) * 8u);
                     }
                     if (c0 + chunk >= kb1) {
-                        const EpiInfo e = get_epi<false>(0, ti.ks, p);
+                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
                         if (p.c_tma) {
 #pragma unroll
                             for (int q = 0; q < PIECES; ++q)
@@ -946,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                        const EpiInfo e = get_epi<false>(0, ti.ks, p);
+                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
                         if (p.c_tma)
                             store_piece_tma(v, slab, row0, col0 + q * 32, ti.ks, e.alpha, &tmC,
                                             lane);
@@ -1031,7 +1033,7 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
-template <int BN, int BK, int NTERMS, bool PROMOTE>
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
 int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
                         TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
     using S = Shape2<BN, BK, NTERMS>;
@@ -1040,7 +1042,7 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
     p.stages = stages;
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
     const int smem = std::max(S::smem_bytes(stages), min_smem);
-    auto kern = tc_gemm_pair_kernel<BN, BK, NTERMS, PROMOTE>;
+    auto kern = tc_gemm_pair_kernel<BN, BK, NTERMS, PROMOTE, GROUPED>;
     static std::atomic<uint64_t> smem_set{0};
     if (!allow_max_smem(kern, smem_set)) return -4;
     int pairs = num_sms / 2;
@@ -1062,12 +1064,18 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
+template <bool GROUPED>
 int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
                   const CUtensorMap& tb, const CUtensorMap& tc, const TcParams& p,
                   const TcLaunch& cfg, int num_sms, cudaStream_t s) {
 #define GB300_PAIR_CASE(BN_, BK_, NT_, PR_)                                                    \
     if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
-        return launch_pair_variant<BN_, BK_, NT_, PR_>(ta, tb, tc, p, cfg, num_sms, s);
+        return launch_pair_variant<BN_, BK_, NT_, PR_, GROUPED>(ta, tb, tc, p, cfg, num_sms, s);
+    if (GROUPED) {  // grouped plans: the split-precision shapes the plan can pick
+        GB300_PAIR_CASE(256, 32, 3, true)
+        GB300_PAIR_CASE(256, 64, 3, true)
+        return -6;
+    }
     GB300_PAIR_CASE(256, 32, 3, true)
     GB300_PAIR_CASE(256, 64, 3, true)
     GB300_PAIR_CASE(256, 32, 3, false)
@@ -1146,10 +1154,12 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-int tc_smem_bytes(int nterms, int bn, int bk, int stages) {
+int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group) {
     const int planes = nterms == 1 ? 1 : 2;
     if ((bn != 128 && bn != 256) || (bk != 32 && bk != 64)) return 0;
-    const int stage = planes * (kBM * bk * 2 + bn * bk * 2);
+    if (cta_group == 2 && bn != 256) return 0;
+    const int b_rows = cta_group == 2 ? bn / 2 : bn;  // a pair stages half of B per CTA
+    const int stage = planes * (kBM * bk * 2 + b_rows * bk * 2);
     return 1024 + stages * stage + 1024 + kEpiWarps * 32 * 33 * 4;
 }
 
@@ -1193,7 +1203,8 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
         p.c_tma = encode_output(&tc, C, M, N, ldc, 1);
     }
     const bool promote = nterms == 3 && cfg.promote_k > 0;
-    const int rc = pair ? dispatch_pair(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream)
+    const int rc = pair ? dispatch_pair<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
+                                               stream)
                         : dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
                                           stream);
     if (rc != 0) return rc;
@@ -1268,6 +1279,9 @@ int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev
     fill_common(p, cfg, bk, nterms, err_word);
     CUtensorMap unused{};  // grouped kernels read their maps from dev_maps
     const bool promote = nterms == 3 && cfg.promote_k > 0;
+    if (cfg.cta_group == 2 && bn == 256)
+        return dispatch_pair<true>(nterms, promote, bn, bk, unused, unused, unused, p, cfg, num_sms,
+                                   stream);
     return dispatch<true>(nterms, promote, bn, bk, unused, unused, unused, p, cfg, num_sms,
                           stream);
 }

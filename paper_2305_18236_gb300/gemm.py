@@ -304,7 +304,7 @@ class GroupedPlan:
               "gemm_grouped_plan_config")
         names = {v: k for k, v in LAYOUTS.items()}
         return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
-                "raster_group": cfg.raster_group,
+                "raster_group": cfg.raster_group, "cta_group": cfg.cta_group,
                 "operand_layout": names.get(cfg.operand_layout, cfg.operand_layout),
                 "tuned_ms": ms.value}
 

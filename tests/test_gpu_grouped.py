@@ -106,6 +106,75 @@ def test_grouped_integer_bit_exact_autotuned_and_fixed():
         assert np.array_equal(b.astype(np.float64), ref)
 
 
+@pytest.mark.parametrize("layout", ["as_stored", "k_major"])
+def test_grouped_cta_pairs_integer_exact(layout):
+    """The grouped launch on CTA pairs (256-row tiles, each CTA staging half
+    of B, per-problem tensor maps): uneven problems with every transpose and
+    ragged edges, exact on integer data, and within bounds on U[-1, 1]."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    h.set_config(cta_group=2, operand_layout=layout)
+    rng = np.random.default_rng(17)
+    probs, dev = [], []
+    for i in range(14):
+        M, N, K = (int(x) for x in rng.integers(40, 700, size=3))
+        tA, tB = bool(i & 1), bool(i & 2)
+        A = inputs.integers((K, M) if tA else (M, K), 900 + 3 * i)
+        B = inputs.integers((N, K) if tB else (K, N), 901 + 3 * i)
+        C0 = inputs.integers((M, N), 902 + 3 * i)
+        probs.append((A, B, C0, tA, tB))
+        dev.append(dict(A=torch.from_numpy(A).cuda(), B=torch.from_numpy(B).cuda(),
+                        C=torch.from_numpy(C0.copy()).cuda(), transA=tA, transB=tB, alpha=1.5,
+                        beta=0.5))
+    plan = g.GroupedPlan(dev, mode="bf16x3", h=h)
+    assert plan.config()["cta_group"] == 2
+    plan.run()
+    torch.cuda.synchronize()
+    for (A, B, C0, tA, tB), d in zip(probs, dev):
+        ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
+        assert np.array_equal(d["C"].cpu().numpy().astype(np.float64), ref)
+    plan.close()
+    fl = make_problems(10, 23)
+    dv = to_device(fl)
+    plan = g.GroupedPlan(dv, mode="bf16x3", h=h)
+    plan.run()
+    check_against_oracle(fl, dv, "bf16x3")
+    plan.close()
+    h.close()
+
+
+def test_grouped_default_configuration_follows_cost_model():
+    """Untuned plans on a handle without tile settings take the cost model's
+    first choice: CTA pairs for many large uneven problems, one CTA per
+    tile when every problem is at most 128 rows tall (a 256-row pair tile
+    would double the padded work); a handle that forces one CTA keeps it."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    def plan_cfg(shapes, h=None):
+        dev = [dict(A=torch.zeros((M, K), device="cuda"), B=torch.zeros((K, N), device="cuda"),
+                    C=torch.zeros((M, N), device="cuda")) for (M, N, K) in shapes]
+        plan = g.GroupedPlan(dev, mode="bf16x3", h=h)
+        cfg = plan.config()
+        plan.close()
+        return cfg
+
+    rng = np.random.default_rng(31)
+    large = [tuple(int(x) * 32 for x in rng.integers(24, 65, size=3)) for _ in range(200)]
+    assert plan_cfg(large)["cta_group"] == 2
+    short = [(int(m), 1024, 1024) for m in rng.integers(16, 129, size=200)]
+    assert plan_cfg(short)["cta_group"] == 1
+    h = g.Gemm()
+    h.set_config(cta_group=1)
+    cfg = plan_cfg(large, h)
+    assert cfg["cta_group"] == 1 and cfg["bk"] == 32
+    h.close()
+
+
 def test_grouped_graph_replay_equals_eager():
     """A graph-captured plan replayed twice on beta = 0 problems equals an
     eager run, bit for bit; with beta != 0 each replay applies the update
