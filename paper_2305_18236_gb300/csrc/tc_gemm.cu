@@ -352,6 +352,25 @@ __device__ __forceinline__ OpLayout op_layout(int mn, int plane_bytes) {
     return l;
 }
 
+// The same in descriptor units: the descriptor of the operand's hi tile in
+// ring slot 0, and what a lo plane and a 16-deep K slice add to it.  The
+// start-address field holds address / 16 in 14 bits and shared memory ends
+// below 2^18 bytes, so adding (offset / 16) to a descriptor never carries out
+// of the field; the MMA issuer builds every descriptor of a stage with adds.
+struct OpDesc {
+    uint64_t d0;
+    uint32_t lo16;
+    uint32_t k16;
+};
+
+__device__ __forceinline__ OpDesc op_desc(uint32_t slot0_addr, const OpLayout& l) {
+    OpDesc d;
+    d.d0 = sdesc_at(slot0_addr, l.fields);
+    d.lo16 = l.lo_off >> 4;
+    d.k16 = l.k_step >> 4;
+    return d;
+}
+
 // TMA copies of one operand's BK-deep slice into a stage: one box for a
 // K-major operand, rows / 64 boxes for an MN-major one.  x coordinates are
 // multiples of BK or of 64 elements (16-byte aligned) and never negative.
@@ -422,13 +441,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t pol = l2_policy_evict_last();
             uint32_t filled = 0;      // bit s: slot s received a fill
             uint32_t fill_par = 0;    // bit s: parity of slot s's latest fill
-            int it = 0;
+            int s = 0;                // ring slot of the next fill
+            uint32_t ph = 0;          // and its parity
             bool ok = true;
             for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
-                for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
-                    const int s = it % stages;
-                    const uint32_t ph = (it / stages) & 1;
+                for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
                     if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                         ok = false;
                         break;
@@ -451,6 +469,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol);
                     filled |= 1u << s;
                     fill_par = (fill_par & ~(1u << s)) | (ph << s);
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
             }
             // Wait for every copy this thread started before the CTA may exit.
@@ -460,15 +482,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            int it = 0, g = 0;  // g: accumulation chunks started by this CTA
+            // One thread issues every MMA, so its per-stage instruction path
+            // is on the critical path of the tensor pipe: ring slot and parity
+            // are running counters and descriptors are built with adds.
+            int g = 0;        // accumulation chunks started by this CTA
+            int s = 0;        // ring slot of the next stage to consume
+            uint32_t ph = 0;  // and its fill parity
             bool ok = true;
+            const uint32_t slot0 = smem_u32(smem);
             for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
                 const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
                 const uint32_t idesc = make_idesc_bf16_f32(kBM, BN, a_mn, b_mn);
-                const OpLayout la = op_layout<S>(a_mn, S::A_PLANE);
-                const OpLayout lb = op_layout<S>(b_mn, S::B_PLANE);
+                const OpDesc da = op_desc(slot0, op_layout<S>(a_mn, S::A_PLANE));
+                const OpDesc db =
+                    op_desc(slot0 + S::PLANES * S::A_PLANE, op_layout<S>(b_mn, S::B_PLANE));
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                     const int buf = g & 1;
@@ -480,34 +509,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + buf * BN;
                     const int c1 = min(c0 + chunk, kb1);
-                    for (int kb = c0; kb < c1; ++kb, ++it) {
-                        const int s = it % stages;
-                        const uint32_t ph = (it / stages) & 1;
+                    for (int kb = c0; kb < c1; ++kb) {
                         if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_st = smem_u32(smem + s * S::STAGE);
-                        const uint32_t b_st = a_st + S::PLANES * S::A_PLANE;
+                        const uint32_t slot16 = uint32_t(s) * uint32_t(S::STAGE >> 4);
+                        const uint64_t a_s = da.d0 + slot16, b_s = db.d0 + slot16;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t a_hi = a_st + kk * la.k_step;
-                            const uint32_t b_hi = b_st + kk * lb.k_step;
+                            const uint64_t ah = a_s + uint32_t(kk) * da.k16;
+                            const uint64_t bh = b_s + uint32_t(kk) * db.k16;
                             const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
                             if (NTERMS == 3) {
-                                umma_bf16(d_tmem, sdesc_at(a_hi + la.lo_off, la.fields),
-                                          sdesc_at(b_hi, lb.fields), idesc, acc);
-                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
-                                          sdesc_at(b_hi + lb.lo_off, lb.fields), idesc, 1u);
-                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
-                                          sdesc_at(b_hi, lb.fields), idesc, 1u);
+                                umma_bf16(d_tmem, ah + da.lo16, bh, idesc, acc);
+                                umma_bf16(d_tmem, ah, bh + db.lo16, idesc, 1u);
+                                umma_bf16(d_tmem, ah, bh, idesc, 1u);
                             } else {
-                                umma_bf16(d_tmem, sdesc_at(a_hi, la.fields),
-                                          sdesc_at(b_hi, lb.fields), idesc, acc);
+                                umma_bf16(d_tmem, ah, bh, idesc, acc);
                             }
                         }
                         umma_commit(&empty[s]);  // slot free once these MMAs have read it
+                        if (++s == stages) {
+                            s = 0;
+                            ph ^= 1;
+                        }
                     }
                     if (!ok) break;
                     umma_commit(&acc_full[buf]);  // chunk ready for the epilogue
@@ -752,13 +779,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             const uint64_t pol = l2_policy_evict_last();
             const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
-            int it = 0;  // stages this producer filled
+            int it = 0;       // stages this producer filled
+            int s = 0;        // ring slot of the next fill
+            uint32_t ph = 0;  // and its parity
             bool ok = true;
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
-                    const int s = it % stages;
-                    const uint32_t ph = (it / stages) & 1;
                     if (!mbar_wait_bounded_cluster(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                         ok = false;
                         break;
@@ -772,6 +799,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     load_operand_pair(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], bar, rank != 0,
                                       (ti.maj >> 1) & 1, S::BNH, S::MN_GROUP, kb * BK,
                                       ti.nt * BN + int(rank) * S::BNH, pol);
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
             }
             if (rank != 0) {
@@ -801,15 +832,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {
             // -------------------------------------------- pair MMA issuer (even CTA)
-            int it = 0, g = 0;
+            // (per-stage path kept short as in the one-CTA issuer)
+            int g = 0;
+            int s = 0;        // ring slot of the next stage to consume
+            uint32_t ph = 0;  // and its fill parity
             bool ok = true;
+            const uint32_t slot0 = smem_u32(smem);
             for (int t = pair; t < p.num_tiles && ok; t += npairs) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
                 const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
                 const uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN, a_mn, b_mn);
-                const OpLayout la = op_layout<S>(a_mn, S::A_PLANE);
-                const OpLayout lb = op_layout<S>(b_mn, S::B_PLANE);
+                const OpDesc da = op_desc(slot0, op_layout<S>(a_mn, S::A_PLANE));
+                const OpDesc db =
+                    op_desc(slot0 + S::PLANES * S::A_PLANE, op_layout<S>(b_mn, S::B_PLANE));
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                     const int buf = g & 1;
@@ -822,34 +858,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + buf * BN;
                     const int c1 = min(c0 + chunk, kb1);
-                    for (int kb = c0; kb < c1; ++kb, ++it) {
-                        const int s = it % stages;
-                        const uint32_t ph = (it / stages) & 1;
+                    for (int kb = c0; kb < c1; ++kb) {
                         if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
                             ok = false;  // both CTAs' halves of stage s are counted on full[s]
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_st = smem_u32(smem + s * S::STAGE);
-                        const uint32_t b_st = a_st + S::PLANES * S::A_PLANE;
+                        const uint32_t slot16 = uint32_t(s) * uint32_t(S::STAGE >> 4);
+                        const uint64_t a_s = da.d0 + slot16, b_s = db.d0 + slot16;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t a_hi = a_st + kk * la.k_step;
-                            const uint32_t b_hi = b_st + kk * lb.k_step;
+                            const uint64_t ah = a_s + uint32_t(kk) * da.k16;
+                            const uint64_t bh = b_s + uint32_t(kk) * db.k16;
                             const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
                             if (NTERMS == 3) {
-                                umma_bf16_pair(d_tmem, sdesc_at(a_hi + la.lo_off, la.fields),
-                                               sdesc_at(b_hi, lb.fields), idesc, acc);
-                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
-                                               sdesc_at(b_hi + lb.lo_off, lb.fields), idesc, 1u);
-                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
-                                               sdesc_at(b_hi, lb.fields), idesc, 1u);
+                                umma_bf16_pair(d_tmem, ah + da.lo16, bh, idesc, acc);
+                                umma_bf16_pair(d_tmem, ah, bh + db.lo16, idesc, 1u);
+                                umma_bf16_pair(d_tmem, ah, bh, idesc, 1u);
                             } else {
-                                umma_bf16_pair(d_tmem, sdesc_at(a_hi, la.fields),
-                                               sdesc_at(b_hi, lb.fields), idesc, acc);
+                                umma_bf16_pair(d_tmem, ah, bh, idesc, acc);
                             }
                         }
                         umma_commit_pair(&empty[s], 0x3);  // both CTAs may refill slot s
+                        if (++s == stages) {
+                            s = 0;
+                            ph ^= 1;
+                        }
                     }
                     if (!ok) break;
                     umma_commit_pair(&acc_full[buf], 0x3);
