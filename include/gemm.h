@@ -85,9 +85,10 @@ typedef struct gemm_context *gemm_handle_t;
  *    accumulation rounds toward zero, so long chains lose accuracy).
  *  cta_group: 1 = one CTA per 128-row tile; 2 = CTA pairs (a cluster of two
  *    SMs shares a 256-row tile, each staging half of B; bn must be 256);
- *    0 = library choice: pairs for GEMM_MODE_BF16X3 in gemm(),
- *    gemm_from_host and gemm_backward when the problem has at least as many
- *    256 x 256 tiles as the GPU has SM pairs, else one CTA per tile;
+ *    0 = library choice: pairs when the problem has at least as many
+ *    256 x 256 tiles as the GPU has SM pairs, for GEMM_MODE_BF16X3 in
+ *    gemm(), gemm_from_host and gemm_backward, and for plain BF16 (gemm_bf16,
+ *    GEMM_MODE_BF16 in gemm()) when K >= 512; else one CTA per tile;
  *    gemm_syr2k always uses one CTA per tile; grouped plans and
  *    gemm_grouped on a handle that sets none of bn, bk, stages and
  *    cta_group take the tile shape, depth and grouping that an analytic cost
