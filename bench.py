@@ -371,6 +371,7 @@ def run_ours(args):
     compare = None
     if not args.no_compare and mode != "f32_simt":
         simt_steps = max(3, min(10, args.steps))
+        h.ensure_workspace(h.workspace_size(g.MODES["f32_simt"], 0, 0, M, N, K))
         for _ in range(2):
             step(g.MODES["f32_simt"])
         torch.cuda.synchronize()

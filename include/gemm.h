@@ -142,10 +142,11 @@ gemm_status_t gemm_destroy(gemm_handle_t handle);
 gemm_status_t gemm_set_config(gemm_handle_t handle, const gemm_config_t *cfg);
 
 /* Bytes of device workspace gemm() needs for this problem and mode with the
- * handle's current configuration (0 for GEMM_MODE_F32_SIMT, except with
- * split-K).  Workspace holds the BF16 split/packed operands (Algorithm 1's
- * APack/BPack buffers) and split-K partial sums.  Returns 0 for invalid
- * arguments. */
+ * handle's current configuration.  Workspace holds the BF16 split/packed
+ * operands (Algorithm 1's APack/BPack buffers) and split-K partial sums; for
+ * GEMM_MODE_F32_SIMT, the FP32 operands packed for the SIMT kernel when
+ * M*N*K >= 2^30 (room for both operands whatever the transposes; 0 below
+ * that size).  Returns 0 for invalid arguments. */
 size_t gemm_workspace_size(gemm_handle_t handle, gemm_mode_t mode, gemm_op_t transA,
                            gemm_op_t transB, int64_t M, int64_t N, int64_t K);
 
@@ -161,7 +162,11 @@ gemm_status_t gemm_set_workspace(gemm_handle_t handle, void *ws, size_t bytes);
  * 11 ldb, 12 beta, 13 C, 14 ldc, 15 mode, 16 stream.
  * A, B, C may have any 4-byte alignment and any valid ld.
  * With a tensor-core mode and no caller workspace, the first call of a new
- * largest size allocates (cudaMalloc) and is therefore not graph-capturable. */
+ * largest size allocates (cudaMalloc) and is therefore not graph-capturable.
+ * GEMM_MODE_F32_SIMT with M*N*K >= 2^30 first transposes each operand stored
+ * K-contiguous (A with transA == N, B with transB == T) into workspace, the
+ * layout its kernel reads fastest; with a caller workspace smaller than
+ * gemm_workspace_size, or no memory for one, it reads them as stored. */
 gemm_status_t gemm(gemm_handle_t handle, gemm_op_t transA, gemm_op_t transB,
                    int64_t M, int64_t N, int64_t K,
                    float alpha, const float *A, int64_t lda,
@@ -302,8 +307,10 @@ gemm_status_t gemm_syr2k(gemm_handle_t handle, gemm_uplo_t uplo, gemm_op_t trans
                          const float *A, int64_t lda, const float *B, int64_t ldb,
                          float beta, float *C, int64_t ldc, gemm_mode_t mode, void *stream);
 
-/* Bytes of workspace gemm_syr2k needs (the split planes of A and B; 0 for
- * GEMM_MODE_F32_SIMT or invalid arguments). */
+/* Bytes of workspace gemm_syr2k needs: the split planes of A and B; for
+ * GEMM_MODE_F32_SIMT with N*N*K >= 2^30, FP32 K x N copies of A and B (used
+ * with trans == N; the kernel reads A and B as stored when there is no room
+ * for them, and below that size the result is 0); 0 for invalid arguments. */
 size_t gemm_syr2k_workspace_size(gemm_handle_t handle, gemm_mode_t mode, gemm_op_t trans,
                                  int64_t N, int64_t K);
 

@@ -292,6 +292,72 @@ bool too_large(int64_t M, int64_t N, int64_t K) {
     return M > lim || N > lim || K > lim;
 }
 
+// FP32 SIMT pack (Algorithm 1's pack step for the SIMT kernel): an operand
+// stored K-contiguous (A with transA == N, B with transB == T) is first
+// transposed into workspace, so the kernel reads both operands with rows
+// along M and N (its fastest form, 74 % of the FP32 peak at 8192^3 against
+// 56-61 % when it transposes K-contiguous rows itself).  Only for problems of
+// at least 2^30 multiply-adds, where the pass costs under 1 % of the GEMM.
+// The workspace size does not depend on the transposes (room for both
+// operands), so one query covers every orientation of a problem.
+struct SimtPack {
+    bool on = false;
+    int64_t lda_p = 0, ldb_p = 0;  // packed strides: K x round4(M), K x round4(N)
+    size_t a_bytes = 0, total = 0;
+};
+
+SimtPack plan_simt_pack(int64_t M, int64_t N, int64_t K) {
+    SimtPack p;
+    if (double(M) * double(N) * double(K) < double(int64_t(1) << 30)) return p;
+    p.on = true;
+    p.lda_p = (M + 3) / 4 * 4;
+    p.ldb_p = (N + 3) / 4 * 4;
+    p.a_bytes = align_up(size_t(K) * size_t(p.lda_p) * 4);
+    p.total = p.a_bytes + align_up(size_t(K) * size_t(p.ldb_p) * 4);
+    return p;
+}
+
+// The pack is an optimisation: without room for it (caller workspace too
+// small, or no memory) the kernel reads the operands as stored.
+bool simt_pack_ws(gemm_context* h, const SimtPack& pk, uint8_t** ws) {
+    *ws = nullptr;
+    if (!pk.on || (h->user_ws && h->user_ws_bytes < pk.total)) return false;
+    return get_ws(h, pk.total, ws) == GEMM_OK && *ws;
+}
+
+gemm_status_t run_simt(gemm_context* h, int transA, int transB, int64_t M, int64_t N, int64_t K,
+                       float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
+                       float beta, float* C, int64_t ldc, cudaStream_t s) {
+    const SimtPack pk = plan_simt_pack(M, N, K);
+    uint8_t* ws = nullptr;
+    const bool pack = (!transA || transB) && simt_pack_ws(h, pk, &ws);
+    int launches = 1;
+    if (pack) {
+        float* ap = reinterpret_cast<float*>(ws);
+        float* bp = reinterpret_cast<float*>(ws + pk.a_bytes);
+        if (!transA) {
+            if (gb300::launch_transpose_f32(K, M, A, lda, ap, pk.lda_p, s) != cudaSuccess)
+                return GEMM_ERR_CUDA;
+            A = ap;
+            lda = pk.lda_p;
+            transA = GEMM_OP_T;
+            ++launches;
+        }
+        if (transB) {
+            if (gb300::launch_transpose_f32(K, N, B, ldb, bp, pk.ldb_p, s) != cudaSuccess)
+                return GEMM_ERR_CUDA;
+            B = bp;
+            ldb = pk.ldb_p;
+            transB = GEMM_OP_N;
+            ++launches;
+        }
+    }
+    h->last_launches = launches;
+    ProfScope prof(h, s);
+    return status_of(
+        gb300::launch_simt_f32(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s));
+}
+
 gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64_t N, int64_t K,
                        float alpha, const float* A, int64_t lda, const float* B, int64_t ldb,
                        float beta, float* C, int64_t ldc, int mode, cudaStream_t s) {
@@ -302,12 +368,8 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
         return status_of(gb300::launch_scale_c(M, N, beta, C, ldc, s));
     }
     if (too_large(M, N, K)) return GEMM_ERR_UNSUPPORTED;
-    if (mode == GEMM_MODE_F32_SIMT) {
-        h->last_launches = 1;
-        ProfScope prof(h, s);
-        return status_of(
-            gb300::launch_simt_f32(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s));
-    }
+    if (mode == GEMM_MODE_F32_SIMT)
+        return run_simt(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
     const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split);
@@ -469,10 +531,11 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
 size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, gemm_op_t transB,
                            int64_t M, int64_t N, int64_t K) {
     if (!h || M < 0 || N < 0 || K < 0) return 0;
-    if (M == 0 || N == 0 || K == 0 || mode == GEMM_MODE_F32_SIMT) return 0;
-    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
+    if (M == 0 || N == 0 || K == 0) return 0;
     if ((transA != GEMM_OP_N && transA != GEMM_OP_T) || (transB != GEMM_OP_N && transB != GEMM_OP_T))
         return 0;
+    if (mode == GEMM_MODE_F32_SIMT) return plan_simt_pack(M, N, K).total;
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const TcLaunch c = plan_tc(h, nterms, M, N, K, Call::Split);
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
@@ -781,8 +844,9 @@ gemm_status_t gemm_backward(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB,
 size_t gemm_syr2k_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t trans, int64_t N,
                                  int64_t K) {
     if (!h || N <= 0 || K <= 0) return 0;
-    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
     if (trans != GEMM_OP_N && trans != GEMM_OP_T) return 0;
+    if (mode == GEMM_MODE_F32_SIMT) return plan_simt_pack(N, N, K).total;
+    if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
     TcLaunch cfg;
     return plan_syr2k(h, mode == GEMM_MODE_BF16X3 ? 3 : 1, trans, N, K, &cfg).bytes;
 }
@@ -815,7 +879,25 @@ gemm_status_t gemm_syr2k(gemm_handle_t h, gemm_uplo_t uplo, gemm_op_t trans, int
     }
     if (too_large(N, N, 2 * K)) return GEMM_ERR_UNSUPPORTED;
     if (mode == GEMM_MODE_F32_SIMT) {
-        h->last_launches = 1;
+        // X, Y stored N x K: packed into K x N copies first (as in gemm()),
+        // and the kernel runs its trans == T form
+        const SimtPack pk = plan_simt_pack(N, N, K);
+        uint8_t* ws = nullptr;
+        int launches = 1;
+        if (trans == GEMM_OP_N && simt_pack_ws(h, pk, &ws)) {
+            float* xp = reinterpret_cast<float*>(ws);
+            float* yp = reinterpret_cast<float*>(ws + pk.a_bytes);
+            if (gb300::launch_transpose_f32(K, N, A, lda, xp, pk.lda_p, s) != cudaSuccess ||
+                gb300::launch_transpose_f32(K, N, B, ldb, yp, pk.ldb_p, s) != cudaSuccess)
+                return GEMM_ERR_CUDA;
+            A = xp;
+            lda = pk.lda_p;
+            B = yp;
+            ldb = pk.ldb_p;
+            trans = GEMM_OP_T;
+            launches = 3;
+        }
+        h->last_launches = launches;
         ProfScope prof(h, s);
         return status_of(gb300::launch_simt_syr2k(tri, trans, N, K, alpha, A, lda, B, ldb, beta, C,
                                                   ldc, s));

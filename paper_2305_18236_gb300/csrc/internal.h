@@ -143,6 +143,10 @@ cudaError_t launch_split_grouped_t(const SplitJob* dev_jobs, const int* dev_tile
 cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16_t* X,
                              int64_t ldx, uint16_t* out, int64_t ldo, cudaStream_t stream);
 
+// Y = X^T in FP32: Y is rows x cols (row stride ldy), X is stored cols x rows.
+cudaError_t launch_transpose_f32(int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                                 float* Y, int64_t ldy, cudaStream_t stream);
+
 // C <- beta * C (C <- 0 when beta == 0, without reading C); uplo 1 / 2
 // restricts it to the lower / upper triangle (diagonal included).
 cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t ldc,

@@ -154,6 +154,48 @@ __global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t co
     }
 }
 
+// Y = X^T in FP32 (Y rows x cols, X stored cols x rows) through a 64 x 64
+// shared-memory tile, both sides coalesced: the pack pass that hands the FP32
+// SIMT kernel operands with rows along M and N.
+__global__ void __launch_bounds__(256) transpose_f32_kernel(int64_t rows, int64_t cols,
+                                                            const float* __restrict__ X,
+                                                            int64_t ldx, float* __restrict__ Y,
+                                                            int64_t ldy, int y_vec) {
+    __shared__ float tile[64][65];
+    const int64_t tiles_r = (rows + 63) / 64;
+    const int64_t tiles_c = (cols + 63) / 64;
+    const int tid = threadIdx.x;
+    for (int64_t tIdx = blockIdx.x; tIdx < tiles_r * tiles_c; tIdx += gridDim.x) {
+        const int64_t r0 = (tIdx % tiles_r) * 64;
+        const int64_t c0 = (tIdx / tiles_r) * 64;
+#pragma unroll
+        for (int pass = 0; pass < 16; ++pass) {
+            const int i = pass * 4 + (tid >> 6);
+            const int j = tid & 63;
+            const int64_t xr = c0 + i, xc = r0 + j;
+            tile[i][j] = (xr < cols && xc < rows) ? X[xr * ldx + xc] : 0.0f;
+        }
+        __syncthreads();
+        // Y row r0 + rr, 4 consecutive columns per thread
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) {
+            const int rr = pass * 16 + (tid >> 4);
+            const int cc = (tid & 15) * 4;
+            const int64_t yr = r0 + rr, yc = c0 + cc;
+            if (yr < rows && yc < cols) {
+                float* dy = Y + yr * ldy + yc;
+                if (y_vec && yc + 4 <= cols) {
+                    *reinterpret_cast<float4*>(dy) = make_float4(
+                        tile[cc][rr], tile[cc + 1][rr], tile[cc + 2][rr], tile[cc + 3][rr]);
+                } else {
+                    for (int q = 0; q < 4 && yc + q < cols; ++q) dy[q] = tile[cc + q][rr];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(256) pack_rows_kernel(int64_t rows, int64_t cols,
                                                         const uint16_t* __restrict__ X, int64_t ldx,
                                                         uint16_t* __restrict__ out, int64_t ldo) {
@@ -447,6 +489,16 @@ cudaError_t launch_pack_bf16(int trans, int64_t rows, int64_t cols, const uint16
         transpose_kernel<uint16_t><<<grid_for(tiles, 1), 256, 0, stream>>>(rows, cols, X, ldx, out,
                                                                            nullptr, ldo);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_f32(int64_t rows, int64_t cols, const float* X, int64_t ldx,
+                                 float* Y, int64_t ldy, cudaStream_t stream) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int y_vec = ((reinterpret_cast<uintptr_t>(Y) & 15) == 0) && (ldy % 4 == 0);
+    const int64_t tiles = ((rows + 63) / 64) * ((cols + 63) / 64);
+    transpose_f32_kernel<<<grid_for(tiles, 1), 256, 0, stream>>>(rows, cols, X, ldx, Y, ldy,
+                                                                  y_vec);
     return cudaGetLastError();
 }
 

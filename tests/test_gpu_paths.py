@@ -148,6 +148,52 @@ def test_backward_matches_oracle_gradient(tA, tB):
     assert oracle.normwise_error(gB.T if tB else gB, dB_op, DB) <= tol_exact("bf16x3", M)
 
 
+@pytest.mark.parametrize("tA,tB,launches", [(False, False, 2), (False, True, 3), (True, False, 1),
+                                             (True, True, 2)])
+def test_simt_pack_integer_exact(tA, tB, launches):
+    """FP32 SIMT with M*N*K >= 2^30 first transposes each K-contiguous operand
+    into workspace (Algorithm 1's pack step), ragged in every dimension and
+    with packed strides rounded up to 4: exact on integer data, with the
+    expected launches.  With a caller workspace that is too small the kernel
+    reads the operands as stored: one launch, the same result."""
+    import torch
+
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 1030, 1037, 1025  # 1.095e9 multiply-adds
+    A = inputs.integers((K, M) if tA else (M, K), 400)
+    B = inputs.integers((N, K) if tB else (K, N), 401)
+    C0 = inputs.integers((M, N), 402)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
+    h = g.Gemm()
+
+    def r256(x):
+        return (x + 255) // 256 * 256
+
+    want = r256(K * ((M + 3) // 4 * 4) * 4) + r256(K * ((N + 3) // 4 * 4) * 4)
+    assert h.workspace_size("f32_simt", tA, tB, M, N, K) == want
+    assert h.workspace_size("f32_simt", tA, tB, 256, 256, 256) == 0
+    out = g.matmul(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(),
+                   C=torch.from_numpy(C0.copy()).cuda(), alpha=1.5, beta=0.5, transA=tA,
+                   transB=tB, mode="f32_simt", h=h)
+    torch.cuda.synchronize()
+    assert h.last_launch_count() == launches
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), ref)
+    h.close()
+    h2 = g.Gemm()
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    assert h2.lib.gemm_set_workspace(h2.h, ctypes.c_void_p(small.data_ptr()), 256) == _lib.GEMM_OK
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.from_numpy(C0.copy()).cuda()
+    st = h2.gemm(tA, tB, M, N, K, 1.5, dA.data_ptr(), dA.stride(0), dB.data_ptr(), dB.stride(0),
+                 0.5, dC.data_ptr(), dC.stride(0), "f32_simt")
+    assert st == _lib.GEMM_OK and h2.sync() == _lib.GEMM_OK
+    assert h2.last_launch_count() == 1
+    assert np.array_equal(dC.cpu().numpy().astype(np.float64), ref)
+    h2.close()
+
+
 def test_argument_errors_report_position():
     """BLAS-style checks: each invalid argument returns GEMM_ERR_ARG with its
     1-based position and launches nothing."""

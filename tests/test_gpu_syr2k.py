@@ -142,6 +142,30 @@ def test_syr2k_layouts_and_small_grid(layout, uplo):
     h.close()
 
 
+@pytest.mark.parametrize("trans,launches", [(False, 3), (True, 1)])
+@pytest.mark.parametrize("uplo", UPLOS)
+def test_syr2k_simt_pack_exact(uplo, trans, launches):
+    """FP32 SIMT SYR2K with N*N*K >= 2^30: operands stored N x K are first
+    transposed into workspace (K x N copies, strides rounded up to 4) and
+    the kernel runs its trans == T form; exact on integer data, nothing
+    outside the triangle touched."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    N, K = 1030, 1025
+    A = inputs.integers((K, N) if trans else (N, K), 361)
+    B = inputs.integers((K, N) if trans else (N, K), 362)
+    C0 = inputs.integers((N, N), 363)
+    Cin = _c_with_nan_outside(C0, uplo)
+    h = g.Gemm()
+    out = _run(A, B, Cin, 1.5, 0.5, uplo, trans, "f32_simt", h=h)
+    assert h.last_launch_count() == launches
+    ref, _, _ = oracle.syr2k(A, B, 1.5, 0.5, C0, uplo=uplo, trans=trans)
+    m = _mask(N, uplo)
+    assert np.array_equal(out[m].astype(np.float64), ref[m])
+    _check_outside(out, Cin, uplo)
+    h.close()
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_syr2k_special_cases(mode):
     """beta == 0 never reads C inside the triangle; alpha == 0 and K == 0
