@@ -121,13 +121,13 @@ int build_tables(const std::vector<HostProb>& ps, const TcLaunch& cfg,
 // divided by the configuration's efficiency: its padded work per second,
 // measured on 512 uneven problems (M, N, K in 32 * U{2..64}, 3xBF16) with the
 // split pass subtracted, relative to the fastest.  Pairs with BK 64 ran at
-// the sustained tensor rate; smaller stages pay a per-stage cost that no
-// padding term shows (pairs with BK 32 at 0.83, one CTA with BN 128 and
-// BK 32 at 0.58), and one CTA is bounded by the SM's operand intake (0.86).
+// the sustained tensor rate; smaller stages pay a per-stage issue cost that
+// no padding term shows (one CTA with BN 128 and BK 32 at 0.68), and one CTA
+// per tile stays below pairs per clock (0.90 with BN 256, BK 32).
 double config_efficiency(int cg, int bn, int bk) {
-    if (cg == 2) return bk == 64 ? 1.00 : 0.83;
-    if (bn == 256) return bk == 32 ? 0.86 : 0.83;
-    return bk == 64 ? 0.73 : 0.58;
+    if (cg == 2) return bk == 64 ? 1.00 : 0.91;
+    if (bn == 256) return bk == 32 ? 0.90 : 0.83;
+    return bk == 64 ? 0.80 : 0.68;
 }
 
 struct Candidate {
