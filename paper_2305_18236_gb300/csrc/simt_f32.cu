@@ -78,6 +78,39 @@ __device__ __forceinline__ void load_slice(const float* __restrict__ X, int64_t 
     }
 }
 
+// 16-byte asynchronous copy global -> shared memory (no registers); bytes
+// beyond `src_bytes` (0..16) are zero-filled and not read.
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const float* src, int src_bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The K slice [k0, k0+BK) of op(X) (R x K) for X stored K x R with 16-byte
+// aligned rows, copied asynchronously into an unpadded [BK][BM] tile: thread
+// t copies rows k0 + (t >> 5) and +8, elements r0 + (t & 31) * 4 .. +3, so a
+// warp moves one 512-byte row segment per copy; ragged edges zero-filled.
+__device__ __forceinline__ void copy_slice_async(const float* __restrict__ X, int64_t ldx, int R,
+                                                 int K, int r0, int k0, float (*S)[BM]) {
+    const int t = threadIdx.x;
+    const int c = (t & 31) * 4;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int kk = (t >> 5) + 8 * h;
+        const int gk = k0 + kk, gr = r0 + c;
+        const int bytes = (gk < K && gr < R) ? min(4, R - gr) * 4 : 0;
+        cp_async_16(&S[kk][c], bytes ? X + int64_t(gk) * ldx + gr : X, bytes);
+    }
+}
+
 // Store the thread's 8 elements into the [BK][BM + PAD] tile (k-major rows).
 template <bool K_CONTIG>
 __device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const Frag& f) {
@@ -102,8 +135,15 @@ __global__ void __launch_bounds__(THREADS, 2)
     // op(B)^T rows (N x K) are K-contiguous when B is stored N x K (transposed).
     constexpr bool A_KC = !TA;
     constexpr bool B_KC = TB;
-    __shared__ __align__(16) float As[2][BK][BM + PAD];
-    __shared__ __align__(16) float Bs[2][BK][BN + PAD];
+    // Both operands stored K x R with aligned rows (the form large problems
+    // get after the pack pass): a three-stage ring filled by asynchronous
+    // copies, which hold no registers.  Otherwise: two stages filled through
+    // a register prefetch, transposing K-contiguous rows on the way.
+    constexpr bool ASYNC = !A_KC && !B_KC && VEC;
+    constexpr int STAGES = ASYNC ? 3 : 2;
+    constexpr int SP = ASYNC ? 0 : PAD;  // cp.async rows need no padding
+    __shared__ __align__(16) float As[STAGES][BK][BM + SP];
+    __shared__ __align__(16) float Bs[STAGES][BK][BN + SP];
 
     const int m0 = blockIdx.y * BM;
     const int n0 = blockIdx.x * BN;
@@ -113,11 +153,16 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int ty = tid >> 4, tx = tid & 15;
     const bool mn_full = (m0 + BM <= M) && (n0 + BN <= N);
 
-    float acc[8][8];
+    // acc2[i][j] holds columns 2j and 2j+1 of accumulator row i: Blackwell's
+    // packed FP32 FMA (two round-to-nearest fused multiply-adds per lane and
+    // instruction) halves the issue slots the rank-1 updates take, so the
+    // fragment loads and loop overhead no longer compete with them.  Each
+    // element sees exactly the FMA chain of the scalar form.
+    float2 acc2[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 4; ++j) acc2[i][j] = make_float2(0.0f, 0.0f);
 
     const int nk1 = (K + BK - 1) / BK;  // slices of one product
     const int nk = UPLO ? 2 * nk1 : nk1;
@@ -130,28 +175,8 @@ __global__ void __launch_bounds__(THREADS, 2)
         lxb = second ? lda : ldb;
         return (second ? kt - nk1 : kt) * BK;
     };
-    Frag fa, fb;
-    {
-        const float *xa, *xb;
-        int64_t lxa, lxb;
-        const int k0 = slice(0, xa, lxa, xb, lxb);
-        load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, mn_full && BK <= K, fa);
-        load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, mn_full && BK <= K, fb);
-    }
-    store_slice<A_KC>(As[0], fa);
-    store_slice<B_KC>(Bs[0], fb);
-    __syncthreads();
-
-    for (int kt = 0; kt < nk; ++kt) {
-        const int cur = kt & 1;
-        if (kt + 1 < nk) {
-            const float *xa, *xb;
-            int64_t lxa, lxb;
-            const int k0 = slice(kt + 1, xa, lxa, xb, lxb);
-            const bool full = mn_full && (k0 + BK <= K);
-            load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, full, fa);
-            load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, full, fb);
-        }
+    // one BK slice of rank-1 updates from ring stage `cur`
+    auto compute = [&](int cur) {
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
@@ -159,17 +184,67 @@ __global__ void __launch_bounds__(THREADS, 2)
             const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
             const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const float2 b2[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w),
+                                  make_float2(b1.x, b1.y), make_float2(b1.z, b1.w)};
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int i = 0; i < 8; ++i) {
+                const float2 ai = make_float2(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc2[i][j] = __ffma2_rn(ai, b2[j], acc2[i][j]);
+            }
         }
-        if (kt + 1 < nk) {
-            store_slice<A_KC>(As[cur ^ 1], fa);
-            store_slice<B_KC>(Bs[cur ^ 1], fb);
+    };
+
+    if constexpr (ASYNC) {
+        auto issue = [&](int kt) {
+            const float *xa, *xb;
+            int64_t lxa, lxb;
+            const int k0 = slice(kt, xa, lxa, xb, lxb);
+            copy_slice_async(xa, lxa, M, K, m0, k0, As[kt % STAGES]);
+            copy_slice_async(xb, lxb, N, K, n0, k0, Bs[kt % STAGES]);
+        };
+#pragma unroll
+        for (int st = 0; st < STAGES - 1; ++st) {
+            if (st < nk) issue(st);
+            cp_async_commit();  // one group per slice, empty past the end
         }
+        for (int kt = 0; kt < nk; ++kt) {
+            cp_async_wait<STAGES - 2>();  // this thread's copies of slice kt landed
+            __syncthreads();  // everyone's copies landed; stage of slice kt-1 is free
+            if (kt + STAGES - 1 < nk) issue(kt + STAGES - 1);
+            cp_async_commit();
+            compute(kt % STAGES);
+        }
+    } else {
+        Frag fa, fb;
+        {
+            const float *xa, *xb;
+            int64_t lxa, lxb;
+            const int k0 = slice(0, xa, lxa, xb, lxb);
+            load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, mn_full && BK <= K, fa);
+            load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, mn_full && BK <= K, fb);
+        }
+        store_slice<A_KC>(As[0], fa);
+        store_slice<B_KC>(Bs[0], fb);
         __syncthreads();
+
+        for (int kt = 0; kt < nk; ++kt) {
+            const int cur = kt & 1;
+            if (kt + 1 < nk) {
+                const float *xa, *xb;
+                int64_t lxa, lxb;
+                const int k0 = slice(kt + 1, xa, lxa, xb, lxb);
+                const bool full = mn_full && (k0 + BK <= K);
+                load_slice<A_KC, VEC>(xa, lxa, M, K, m0, k0, full, fa);
+                load_slice<B_KC, VEC>(xb, lxb, N, K, n0, k0, full, fb);
+            }
+            compute(cur);
+            if (kt + 1 < nk) {
+                store_slice<A_KC>(As[cur ^ 1], fa);
+                store_slice<B_KC>(Bs[cur ^ 1], fb);
+            }
+            __syncthreads();
+        }
     }
 
     // epilogue: C = alpha * acc + beta * C (C not read when beta == 0)
@@ -183,7 +258,10 @@ __global__ void __launch_bounds__(THREADS, 2)
             const int col = n0 + (h == 0 ? tx * 4 : 64 + tx * 4);
             float o[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) o[j] = alpha * acc[i][h * 4 + j];
+            for (int j = 0; j < 4; ++j) {
+                const float2 pr = acc2[i][(h * 4 + j) >> 1];
+                o[j] = alpha * (((h * 4 + j) & 1) ? pr.y : pr.x);
+            }
             // SYR2K: the 4-wide group is wholly inside the triangle, or is
             // stored element by element
             const bool whole = UPLO == 0 || (UPLO == 1 ? col + 3 <= row : col >= row);
