@@ -24,7 +24,8 @@
 //
 // Warp roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
 // MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31
-// and one half of the tile's columns).
+// and one half of the tile's columns); the plain-BF16 CTA-pair kernel adds
+// warp 10, which issues the B copies (352 threads).
 // Two accumulators (2 x BN TMEM columns) let the epilogue of tile i overlap
 // the MMAs of tile i+1.  Every wait is bounded (ptx.cuh); on expiry the
 // kernel records the error, drains its own copies and MMAs, frees TMEM and
