@@ -194,6 +194,36 @@ def test_simt_pack_integer_exact(tA, tB, launches):
     h2.close()
 
 
+@pytest.mark.parametrize("M,N,K", [(4, 8, 3), (128, 128, 16), (132, 260, 17), (256, 4, 1),
+                                   (516, 388, 1000)])
+def test_simt_async_ring_edges_exact(M, N, K):
+    """The SIMT kernel's asynchronous-copy ring (A stored K x M, B stored
+    K x N, 16-byte aligned rows): K shorter than one 16-deep slice, exact
+    tiles, ragged tiles and a K that leaves a partial last slice, exact on
+    integer data; beta = 0 with NaN in C never reads C."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    A = inputs.integers((K, M), 410)
+    B = inputs.integers((K, N), 411)
+    C0 = inputs.integers((M, N), 412)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=True)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    assert dA.stride(0) % 4 == 0 and dB.stride(0) % 4 == 0
+    h = g.Gemm()
+    out = g.matmul(dA, dB, C=torch.from_numpy(C0.copy()).cuda(), alpha=1.5, beta=0.5,
+                   transA=True, mode="f32_simt", h=h)
+    torch.cuda.synchronize()
+    assert h.last_launch_count() == 1
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), ref)
+    nan_c = torch.full((M, N), float("nan"), device="cuda")
+    out = g.matmul(dA, dB, C=nan_c, transA=True, mode="f32_simt", h=h)
+    ref0, _, _ = oracle.gemm(A, B, transA=True)
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), ref0)
+    h.close()
+
+
 def test_argument_errors_report_position():
     """BLAS-style checks: each invalid argument returns GEMM_ERR_ARG with its
     1-based position and launches nothing."""
