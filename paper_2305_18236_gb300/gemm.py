@@ -30,6 +30,8 @@ def _ld(t):
     """Row stride of a 2-D row-major tensor (last dim contiguous)."""
     if t.dim() != 2:
         raise ValueError("expected a 2-D tensor")
+    if t.numel() == 0:
+        return max(1, t.size(1))  # nothing is read or written: any valid stride
     if t.size(1) > 1 and t.stride(1) != 1:
         raise ValueError("the last dimension must be contiguous (row-major storage)")
     return t.stride(0) if t.size(0) > 1 else max(1, t.size(1))
