@@ -176,3 +176,33 @@ def test_random_grouped_exact(case):
         assert np.array_equal(d["C"].cpu().numpy().astype(np.float64), ref), (mode, cfg)
     plan.close()
     h.close()
+
+
+@pytest.mark.parametrize("case", range(24))
+def test_random_float_within_bounds(case):
+    """U[-1, 1] or log-uniform data under random configurations that keep the
+    accumulation structure (no split-K, default promotion): normwise error
+    against the exact oracle within the mode's bound, and against the
+    oracle's GEMM of the same BF16 products within the accumulation bound."""
+    from tests.gpu_util import TERMS, make_problem, oracle_ref, run_mode, tol_exact, tol_terms
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    rng = np.random.default_rng(9900 + case)
+    mode = ["f32_simt", "bf16", "bf16x3"][case % 3]
+    tA, tB = bool(rng.integers(2)), bool(rng.integers(2))
+    M, N, K = _size(rng), _size(rng), _size(rng)
+    dist = ["uniform", "log_uniform"][int(rng.integers(2))]
+    cfg = [{}, {"cta_group": 2}, {"cta_group": 1, "bn": 128}, {"cta_group": 1, "bk": 64},
+           {"operand_layout": "as_stored"}, {"max_ctas": 7}][int(rng.integers(6))]
+    A, B, C0 = make_problem(M, N, K, tA, tB, dist=dist, seed=9900 + 5 * case, beta=0.5)
+    h = g.Gemm()
+    h.set_config(**cfg)
+    C = run_mode(mode, A, B, 1.5, 0.5, C0, tA, tB, h=h)
+    assert h.sync() == 0
+    C64, D = oracle_ref(A, B, 1.5, 0.5, C0, tA, tB)
+    assert oracle.normwise_error(C, C64, D) <= tol_exact(mode, K), (mode, M, N, K, dist, cfg)
+    if mode in TERMS:
+        T64 = oracle.gemm_split_terms(A, B, TERMS[mode], 1.5, 0.5, C0, transA=tA, transB=tB)
+        assert oracle.normwise_error(C, T64, D) <= tol_terms(mode, K), (mode, M, N, K, dist, cfg)
+    h.close()
