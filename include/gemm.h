@@ -73,7 +73,13 @@ typedef enum {
 typedef struct gemm_context *gemm_handle_t;
 
 /* Launch configuration overrides (all 0 = library choice).
- *  bn:        tensor-core tile width in N (128 or 256); the tile height is 128.
+ *  bn:        tensor-core tile width in N (128 or 256; the tile height is 128,
+ *             256 on CTA pairs), or 512: 256 x 512 pair tiles for plain BF16
+ *             (gemm_bf16, GEMM_MODE_BF16 in gemm()) with BK 64 -- other calls
+ *             use 256 -- which the library also picks for those calls when
+ *             beta == 0 and the problem has a 256 x 512 tile per SM pair and
+ *             K >= 8192, or K >= 2048 with B read in place as MN-major tiles;
+ *             bn 512 with cta_group 1 or bk 32 is GEMM_ERR_ARG.
  *  bk:        K depth of one pipeline stage (32 or 64 BF16 elements).
  *  stages:    shared-memory ring depth (2..8; clamped to what fits).
  *  split_k:   number of K slices reduced by a second kernel (1 = none).

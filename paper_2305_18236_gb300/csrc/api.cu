@@ -94,7 +94,7 @@ bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
 //    and always in grouped plans and SYR2K, whose transposing passes cost
 //    more than the kernel gains.
 TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K, Call call,
-                 bool pack_a = false, bool pack_b = false) {
+                 bool pack_a = false, bool pack_b = false, bool beta_zero = false) {
     TcLaunch c;
     c.bn = h->cfg.bn ? h->cfg.bn : 256;
     if (call == Call::Syr2k) {
@@ -110,7 +110,7 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
         const bool pair_kind = (nterms == 3 && call == Call::Split) ||
                                (nterms == 1 && (call == Call::Split || call == Call::Bf16) &&
                                 K >= 512);
-        c.cta_group = (pair_kind && c.bn == 256 && h->cfg.split_k <= 1 &&
+        c.cta_group = (pair_kind && c.bn >= 256 && h->cfg.split_k <= 1 &&
                        pair_tiles >= h->num_sms / 2)
                           ? 2
                           : 1;
@@ -124,6 +124,23 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
                        : call == Call::Bf16 ? (pack_pays(M, N, K, pack_a, pack_b) ? 1 : 0)
                                             : 0;
     }
+    // 256 x 512 pair tiles (plain BF16): two MMAs share each staged A tile, so
+    // a stage moves a third fewer bytes per flop through shared memory, but
+    // their two accumulators fill the tensor memory and the epilogue no longer
+    // overlaps the next tile's MMAs.  Measured against 256-wide pair tiles
+    // with beta == 0 (TMA-store epilogue): 5-6 % faster at K = 8192, 10-12 %
+    // faster at K = 4096 with B read MN-major in place, up to 5 % slower at
+    // K = 4096 with K-major B and 11-18 % slower at K = 1024; with beta != 0
+    // the drain waits on reads of C and 8192^3 is 15 % slower, so the
+    // library takes them only for beta == 0.
+    const bool wide_ok = c.cta_group == 2 && nterms == 1 && c.bk == 64 &&
+                         (call == Call::Split || call == Call::Bf16);
+    const bool b_in_place_mn = call == Call::Bf16 && !c.kmajor && pack_b;
+    if (h->cfg.bn == 0 && wide_ok && beta_zero &&
+        (K >= 8192 || (K >= 2048 && b_in_place_mn)) &&
+        ((M + 255) / 256) * ((N + 511) / 512) >= h->num_sms / 2)
+        c.bn = 512;
+    if (c.bn == 512 && !wide_ok) c.bn = 256;
     c.stages = h->cfg.stages;
     c.raster_group = h->cfg.raster_group ? h->cfg.raster_group : 16;
     c.max_ctas = h->cfg.max_ctas;
@@ -372,7 +389,7 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
         return run_simt(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
-    const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split);
+    const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split, false, false, beta == 0.0f);
     // op(A) is M x K and op(B)^T is N x K, split K-major or as stored
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
@@ -515,7 +532,8 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         return GEMM_OK;
     }
     const gemm_config_t& c = *cfg;
-    if ((c.bn != 0 && c.bn != 128 && c.bn != 256) || (c.bk != 0 && c.bk != 32 && c.bk != 64) ||
+    if ((c.bn != 0 && c.bn != 128 && c.bn != 256 && c.bn != 512) ||
+        (c.bk != 0 && c.bk != 32 && c.bk != 64) || (c.bn == 512 && (c.cta_group == 1 || c.bk == 32)) ||
         c.stages < 0 || c.stages > 8 || c.stages == 1 || c.split_k < 0 || c.split_k > 64 ||
         c.raster_group < 0 || c.max_ctas < 0 || c.promote_k < -1 || c.cta_group < 0 ||
         c.cta_group > 2 || (c.cta_group == 2 && c.bn == 128) ||
@@ -582,7 +600,7 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
     // place as MN-major tiles, or packed K-contiguous first when the plan
     // wants K-major operands.
     const bool a_kr = transA == GEMM_OP_T, b_kr = transB == GEMM_OP_N;  // stored K x rows
-    const TcLaunch cfg = plan_tc(h, 1, M, N, K, Call::Bf16, a_kr, b_kr);
+    const TcLaunch cfg = plan_tc(h, 1, M, N, K, Call::Bf16, a_kr, b_kr, beta == 0.0f);
     auto misaligned = [](const void* p, int64_t ld) {
         return (reinterpret_cast<uintptr_t>(p) & 15) != 0 || ld % 8 != 0;
     };

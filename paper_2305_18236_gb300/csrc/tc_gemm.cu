@@ -693,9 +693,19 @@ struct Shape2 {
     static constexpr int A_PLANE = kBM * BK * 2;
     static constexpr int B_PLANE = BNH * BK * 2;
     static constexpr int STAGE = PLANES * (A_PLANE + B_PLANE);
-    static constexpr int TMEM_COLS = 2 * BN;
+    // BN 512 (plain BF16): two N = 256 MMAs per 16-deep slice into two
+    // accumulators that fill the tensor memory, so one buffer, not two
+    static constexpr int MMA_N = BN > 256 ? 256 : BN;
+    static constexpr int NSUB = BN / MMA_N;
+    static constexpr int NBUF = BN > 256 ? 1 : 2;
+    static constexpr int TMEM_COLS = NBUF * BN;
     static constexpr int ROW_BYTES = BK * 2;
     static constexpr int MN_GROUP = PLANES * BK * 128;  // as in Shape
+    // offset of the second MMA's B rows inside a CTA's B box: 128 rows,
+    // K-major (128 rows of ROW_BYTES) or MN-major (two 64-row groups)
+    static constexpr int SUB_B = 128 * BK * 2 * PLANES;
+    static_assert(NSUB == 1 || (PLANES == 1 && SUB_B == 2 * MN_GROUP),
+                  "wide pair tiles are plain BF16 only");
     static constexpr int BAR_BYTES = 1024;
     static constexpr int STAGING = kEpiWarps * 32 * 33 * 4;
     static_assert(B_PLANE % 1024 == 0, "B plane must keep swizzle atoms aligned");
@@ -705,6 +715,15 @@ struct Shape2 {
         return s > 8 ? 8 : s;
     }
 };
+
+// Tile column of accumulator column c in a 512-wide pair tile: MMA j takes
+// rows 128j.. of each CTA's 256-row B box (the even CTA's box holds tile
+// columns 0..255, the odd CTA's 256..511), so its accumulator holds tile
+// columns 128j + [0, 128) and then 256 + 128j + [0, 128).
+__device__ __forceinline__ int wide_tile_col(int c) {
+    const int j = c >> 8, w = c & 255;
+    return w < 128 ? j * 128 + w : 256 + j * 128 + (w - 128);
+}
 
 // The pair form of load_operand: the even CTA's copies count on its own full
 // barrier, the odd CTA's on the even CTA's (`peer_bar`, cta_group::2 form).
@@ -892,14 +911,14 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int kb0 = ti.kb0, kb1 = ti.kb1;
                 const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
-                const uint32_t idesc = make_idesc_bf16_f32(2 * kBM, BN, a_mn, b_mn);
+                const uint32_t idesc = make_idesc_bf16_f32(2 * kBM, S::MMA_N, a_mn, b_mn);
                 const OpDesc da = op_desc(slot0, op_layout<S>(a_mn, S::A_PLANE));
                 const OpDesc db =
                     op_desc(slot0 + S::PLANES * S::A_PLANE, op_layout<S>(b_mn, S::B_PLANE));
                 const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                 for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
-                    const int buf = g & 1;
-                    const uint32_t acc_ph = (g >> 1) & 1;
+                    const int buf = S::NBUF == 2 ? (g & 1) : 0;
+                    const uint32_t acc_ph = (S::NBUF == 2 ? (g >> 1) : g) & 1;
                     if (!mbar_wait_bounded_cluster(&acc_empty[buf], acc_ph ^ 1, p.lim, abort_flag,
                                                    p.err)) {
                         ok = false;
@@ -926,7 +945,10 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                                 umma_bf16_pair(d_tmem, ah, bh + db.lo16, idesc, 1u);
                                 umma_bf16_pair(d_tmem, ah, bh, idesc, 1u);
                             } else {
-                                umma_bf16_pair(d_tmem, ah, bh, idesc, acc);
+#pragma unroll
+                                for (int j = 0; j < S::NSUB; ++j)
+                                    umma_bf16_pair(d_tmem + j * S::MMA_N, ah,
+                                                   bh + uint32_t(j) * (S::SUB_B >> 4), idesc, acc);
                             }
                         }
                         umma_commit_pair(&empty[s], 0x3);  // both CTAs may refill slot s
@@ -967,8 +989,8 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
             const int col0 = ti.nt * BN + col_base;
 #pragma unroll 1
             for (int c0 = kb0; c0 < kb1; c0 += chunk, ++g) {
-                const int buf = g & 1;
-                const uint32_t acc_ph = (g >> 1) & 1;
+                const int buf = S::NBUF == 2 ? (g & 1) : 0;
+                const uint32_t acc_ph = (S::NBUF == 2 ? (g >> 1) : g) & 1;
                 int got = 0;
                 if (lane == 0)
                     got = mbar_wait_bounded_cluster(&acc_full[buf], acc_ph, p.lim, abort_flag,
@@ -980,8 +1002,17 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (uint32_t(ew * 32) << 16) + buf * BN + col_base;
-                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1)
-                    prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0, col0, COLS, lane);
+                if (c0 + 2 * chunk >= kb1 && c0 + chunk < kb1) {
+                    if (S::NSUB == 1) {
+                        prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0, col0, COLS, lane);
+                    } else {
+                        const int tc0 = ti.nt * BN;
+                        prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0,
+                                   tc0 + wide_tile_col(col_base), 128, lane);
+                        prefetch_c(get_epi<GROUPED>(ti.prob, ti.ks, p), row0,
+                                   tc0 + wide_tile_col(col_base + 128), 128, lane);
+                    }
+                }
                 if (PROMOTE) {
                     if (c0 == kb0) {
 #pragma unroll
@@ -1033,11 +1064,13 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
                         const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
+                        // 32-column pieces never cross a 128-column block
+                        const int col = S::NSUB == 1 ? col0 + q * 32
+                                                     : ti.nt * BN + wide_tile_col(col_base + q * 32);
                         if (p.c_tma)
-                            store_piece_tma(v, slab, row0, col0 + q * 32, ti.ks, e.alpha, &tmC,
-                                            lane);
+                            store_piece_tma(v, slab, row0, col, ti.ks, e.alpha, &tmC, lane);
                         else
-                            store_piece(v, stg, row0, col0 + q * 32, e, lane);
+                            store_piece(v, stg, row0, col, e, lane);
                     }
                     tc_fence_before();
                     __syncwarp();
@@ -1165,6 +1198,7 @@ int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& t
     GB300_PAIR_CASE(256, 32, 3, false)
     GB300_PAIR_CASE(256, 64, 1, false)
     GB300_PAIR_CASE(256, 32, 1, false)
+    GB300_PAIR_CASE(512, 64, 1, false)
 #undef GB300_PAIR_CASE
     return -6;
 }
@@ -1240,8 +1274,9 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
 
 int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group) {
     const int planes = nterms == 1 ? 1 : 2;
-    if ((bn != 128 && bn != 256) || (bk != 32 && bk != 64)) return 0;
-    if (cta_group == 2 && bn != 256) return 0;
+    if ((bn != 128 && bn != 256 && bn != 512) || (bk != 32 && bk != 64)) return 0;
+    if (cta_group == 2 && bn == 128) return 0;
+    if (bn == 512 && (cta_group != 2 || nterms != 1 || bk != 64)) return 0;
     const int b_rows = cta_group == 2 ? bn / 2 : bn;  // a pair stages half of B per CTA
     const int stage = planes * (kBM * bk * 2 + b_rows * bk * 2);
     return 1024 + stages * stage + 1024 + kEpiWarps * 32 * 33 * 4;
@@ -1252,9 +1287,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
                    const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
                    int* launches) {
     if (M > (1ll << 31) - 256 || N > (1ll << 31) - 256 || K > (1ll << 31) - 256) return -6;
-    const int bn = cfg.bn == 128 ? 128 : 256;
-    const int bk = cfg.bk == 64 ? 64 : 32;
-    const bool pair = cfg.cta_group == 2 && bn == 256;
+    // 512-wide tiles exist for plain BF16 on CTA pairs with BK 64 only
+    const bool wide = cfg.bn == 512 && cfg.cta_group == 2 && nterms == 1 && cfg.bk != 32;
+    const int bn = wide ? 512 : cfg.bn == 128 ? 128 : 256;
+    const int bk = wide ? 64 : cfg.bk == 64 ? 64 : 32;
+    const bool pair = cfg.cta_group == 2 && bn >= 256;
     const int bm = pair ? 2 * kBM : kBM;  // output rows per tile (per CTA pair)
     TcParams p{};
     p.maj = (a.mn_major ? 1 : 0) | (b.mn_major ? 2 : 0);

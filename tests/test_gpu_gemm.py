@@ -235,9 +235,65 @@ def test_cta_pair_kernel(mode, bk, split):
     h.close()
 
 
-@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("beta", [0.0, 0.5])
 @pytest.mark.parametrize("layout", ["k_major", "as_stored"])
-def test_cta_pair_timeout_path(layout, mode):
+@pytest.mark.parametrize("tB", [False, True])
+def test_wide_pair_tiles_exact(tB, layout, beta):
+    """256 x 512 pair tiles (plain BF16, two MMAs per slice into two
+    accumulators, one accumulator buffer): ragged M, N, K (none a multiple
+    of its tile size), both B orientations and operand layouts, beta 0 (TMA
+    store epilogue) and not, exact on integer data, through gemm() in BF16
+    mode and through gemm_bf16; split-K partial tiles too."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    M, N, K = 600, 1096, 776  # ld % 8 == 0 (gemm_bf16 reads operands in place); ragged tiles
+    A = inputs.integers((M, K), 86)
+    B = inputs.integers((N, K) if tB else (K, N), 87)
+    C0 = inputs.integers((M, N), 88)
+    ref, _, _ = oracle.gemm(A, B, 1.5, beta, C0, transB=tB)
+    for split in (1, 3):
+        h = g.Gemm()
+        h.set_config(bn=512, cta_group=2, operand_layout=layout, split_k=split)
+        C = run_mode("bf16", A, B, 1.5, beta, C0, False, tB, h=h)
+        assert np.array_equal(C.astype(np.float64), ref), split
+        h.close()
+    h = g.Gemm()
+    h.set_config(bn=512, cta_group=2, operand_layout=layout)
+    dC = torch.from_numpy(C0.copy()).cuda()
+    g.matmul_bf16(torch.from_numpy(A).cuda().to(torch.bfloat16),
+                  torch.from_numpy(B).cuda().to(torch.bfloat16), C=dC, alpha=1.5, beta=beta,
+                  transB=tB, h=h)
+    torch.cuda.synchronize()
+    assert np.array_equal(dC.cpu().numpy().astype(np.float64), ref)
+    h.close()
+
+
+def test_wide_pair_tile_config_validation():
+    """bn 512 exists only on CTA pairs with BK 64: other combinations are
+    rejected at gemm_set_config (argument 2); with 3xBF16 the handle's bn 512
+    runs 256-wide tiles."""
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+
+    h = g.Gemm()
+    for bad in (dict(bn=512, cta_group=1), dict(bn=512, bk=32), dict(bn=384)):
+        with pytest.raises(_lib.GemmError) as e:
+            h.set_config(**bad)
+        assert e.value.status == _lib.GEMM_ERR_ARG and h.last_error_arg() == 2
+    h.set_config(bn=512)
+    Ai = inputs.integers((300, 500), 89)
+    Bi = inputs.integers((500, 700), 90)
+    C = run_mode("bf16x3", Ai, Bi, 1.0, 0.0, None, False, False, h=h)
+    ref, _, _ = oracle.gemm(Ai, Bi)
+    assert np.array_equal(C.astype(np.float64), ref)
+    h.close()
+
+
+@pytest.mark.parametrize("mode,bn", [("bf16", 256), ("bf16x3", 256), ("bf16", 512)])
+@pytest.mark.parametrize("layout", ["k_major", "as_stored"])
+def test_cta_pair_timeout_path(layout, mode, bn):
     """The pair kernel's bounded waits expire cleanly too (one-poll limit):
     the even producer settles the stages each CTA filled, every copy lands
     before either CTA leaves, and the next call on the context is correct."""
@@ -247,13 +303,13 @@ def test_cta_pair_timeout_path(layout, mode):
     from paper_2305_18236_gb300 import gemm as g
 
     h = g.Gemm()
-    h.set_config(bn=256, cta_group=2, wait_poll_limit=1, operand_layout=layout)
+    h.set_config(bn=bn, cta_group=2, wait_poll_limit=1, operand_layout=layout)
     A, B, _ = make_problem(1024, 1024, 2048, seed=85)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
     C = torch.zeros((1024, 1024), device="cuda")
     g.matmul(dA, dB, C=C, mode=mode, h=h)
     assert h.sync() == _lib.GEMM_ERR_TIMEOUT
-    h.set_config(bn=256, cta_group=2, operand_layout=layout)
+    h.set_config(bn=bn, cta_group=2, operand_layout=layout)
     g.matmul(dA, dB, C=C, mode=mode, h=h)
     assert h.sync() == _lib.GEMM_OK
     rows = np.arange(0, 1024, 101)

@@ -21,6 +21,7 @@ CONFIGS = [
     {"operand_layout": "k_major", "cta_group": 2},
     {"operand_layout": "as_stored", "cta_group": 2, "bk": 32},
     {"raster_group": 1, "max_ctas": 5},
+    {"cta_group": 2, "bn": 512},
 ]
 ALPHAS = [1.0, 1.5, -0.5, 0.0]
 BETAS = [0.0, 1.0, 0.5]
