@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import LAYOUTS, MODES, OP_N, OP_T, check, gemm_config_t, gemm_problem_t
+from ._lib import LAYOUTS, MODES, check, gemm_config_t, gemm_problem_t
 
 __all__ = ["Gemm", "handle", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
            "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "sync"]
