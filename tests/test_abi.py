@@ -83,3 +83,24 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_LIB", None)
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_binding_row_stride_of_tensors():
+    """The binding's row stride: row-major tensors give their row stride,
+    a one-row tensor its width, and empty tensors (whose strides torch may
+    report as 0) any valid stride; a non-contiguous last dimension raises."""
+    import numpy as np
+    import torch
+
+    from paper_2305_18236_gb300.gemm import _ld
+
+    assert _ld(torch.zeros((3, 4))) == 4
+    assert _ld(torch.zeros((8, 6))[:, :5]) == 6
+    assert _ld(torch.zeros((1, 7))) == 7
+    for shape, want in [((0, 5), 5), ((5, 0), 1), ((0, 0), 1)]:
+        t = torch.from_numpy(np.zeros(shape, np.float32))
+        assert _ld(t) == want
+    with pytest.raises(ValueError):
+        _ld(torch.zeros((4, 6)).t())
+    with pytest.raises(ValueError):
+        _ld(torch.zeros(4))
