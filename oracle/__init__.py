@@ -17,7 +17,10 @@ loop nest computes alpha * op(A) op(B) + beta * C with beta applied once):
   the rank-2k update of Section 6.1 (exact or with split products).
 * ``normwise_error`` -- max |C - C64| / max D, the error measure.
 
-Every function is pinned by ``tests/test_oracle_pins.py``; none is unpinned.
+Every function is pinned by ``tests/test_oracle_pins.py`` (the checks in
+``tests/oracle_pins.py``), ``normwise_error`` included (hand-computed cases);
+``tests/test_oracle_mutants.py`` plants mistakes in ``gemm_ref.c`` and in
+``normwise_error`` and each one fails a pin.
 """
 import ctypes
 import os

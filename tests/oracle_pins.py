@@ -189,6 +189,37 @@ def check_denominator(orc):
     assert np.array_equal(D, ref)
 
 
+
+def check_normwise_error(orc):
+    """The error measure max_ij |C - C64| / max_ij D on hand-computed cases.
+
+    Case 1 (2 x 3): |C - C64| = [[0, 1.5, 0], [0, 0, 1]] (the larger
+    deviation is negative), max D = 8, so the error is 1.5 / 8 = 0.1875;
+    a mean in place of a max, an element-wise ratio (0.5), a signed
+    difference (1/8), D at the worst element (1.5/4) or no denominator all
+    give other values.  Row subsets take the max over their own rows only.
+    The difference is formed in FP64 (a 2**-30 gap survives), a NaN in C
+    gives NaN (it is within no tolerance), a zero numerator gives 0 even
+    when D vanishes, and a nonzero numerator over D = 0 gives inf."""
+    C = np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]], np.float32)
+    C64 = np.array([[1.0, 3.5, 3.0], [4.0, 5.0, 5.0]], np.float64)
+    D = np.array([[2.0, 4.0, 1.0], [8.0, 3.0, 2.0]], np.float64)
+    assert orc.normwise_error(C, C64, D) == 0.1875
+    assert orc.normwise_error(C[[1]], C64[[1]], D[[1]]) == 1.0 / 8.0
+    assert orc.normwise_error(C[[0]], C64[[0]], D[[0]]) == 1.5 / 4.0
+    assert orc.normwise_error(C[:, [0, 2]], C64[:, [0, 2]], D[:, [0, 2]]) == 1.0 / 8.0
+    one = np.ones((1, 1), np.float32)
+    gap = np.array([[1.0 + 2.0 ** -30]])
+    assert orc.normwise_error(one, gap, np.ones((1, 1))) == 2.0 ** -30
+    nan_c = C.copy()
+    nan_c[0, 0] = np.nan
+    assert np.isnan(orc.normwise_error(nan_c, C64, D))
+    assert orc.normwise_error(C, C.astype(np.float64), np.zeros((2, 3))) == 0.0
+    assert orc.normwise_error(C, C64, np.zeros((2, 3))) == float("inf")
+    empty = np.zeros((0, 3))
+    assert orc.normwise_error(empty.astype(np.float32), empty, empty) == 0.0
+
+
 def _edge_values():
     bits = np.array([
         0x00000000, 0x80000000, 0x3f800000, 0xbf800000,   # +-0, +-1
@@ -463,6 +494,7 @@ def check_syr2k_split_terms(orc):
 ALL_CHECKS = [check_brute_force, check_identity, check_permutation, check_all_ones,
               check_integers, check_transpose_identity, check_blocked_k,
               check_alpha_beta_special, check_rows_subset, check_denominator,
+              check_normwise_error,
               check_split_vs_library, check_split_invariants,
               check_split_terms_brute_force, check_split_terms_reduce,
               check_syr2k_brute_force, check_syr2k_vs_library, check_syr2k_integers,

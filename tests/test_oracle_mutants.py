@@ -81,3 +81,46 @@ def test_mutant_is_caught(name, tmp_path):
         return  # the mutant crashed on a pin input: caught
     line = [l for l in res.stdout.splitlines() if l.startswith("FAILED:")][-1]
     assert line != "FAILED:", "mutant %s passed every pin" % name
+
+
+# Planted mistakes in the error measure (Python, so they are applied to a
+# copy of the function's source rather than to gemm_ref.c).
+ERROR_MUTANTS = {
+    "returns_zero": ("    if num == 0.0:\n        return 0.0", "    if True:\n        return 0.0"),
+    "mean_for_max": ("num = float(np.max(np.abs(C - C64)))", "num = float(np.mean(np.abs(C - C64)))"),
+    "elementwise_ratio": ("num = float(np.max(np.abs(C - C64))) if C.size else 0.0\n    den = float(np.max(D))",
+                          "num = float(np.max(np.abs(C - C64) / np.where(D > 0, D, 1.0))) if C.size else 0.0\n    den = 1.0 or float(np.max(D))"),
+    "denominator_dropped": ("    return num / den", "    return num"),
+    "denominator_ignores_d": ("den = float(np.max(D))", "den = float(np.max(np.abs(C64)))"),
+    "signed_difference": ("num = float(np.max(np.abs(C - C64)))", "num = float(np.max(C - C64))"),
+    "nan_ignored": ("num = float(np.max(np.abs(C - C64)))", "num = float(np.nanmax(np.abs(C - C64)))"),
+    "difference_in_f32": ("C = np.asarray(C, dtype=np.float64)",
+                          "C = np.asarray(C, dtype=np.float32); C64 = np.asarray(C64, dtype=np.float32)"),
+    "mean_denominator": ("den = float(np.max(D))", "den = float(np.mean(D))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ERROR_MUTANTS))
+def test_error_measure_mutant_is_caught(name):
+    import inspect
+    import types
+
+    import numpy as np
+
+    import oracle
+    from tests import oracle_pins
+
+    old, new = ERROR_MUTANTS[name]
+    src = inspect.getsource(oracle.normwise_error)
+    assert src.count(old) == 1, "mutation anchor not found: %s" % name
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    orc = types.SimpleNamespace(**{n: getattr(oracle, n) for n in dir(oracle) if not n.startswith("__")})
+    orc.normwise_error = ns["normwise_error"]
+    failed = []
+    for check in oracle_pins.ALL_CHECKS:
+        try:
+            check(orc)
+        except Exception:
+            failed.append(check.__name__)
+    assert failed, "error-measure mutant %s passed every pin" % name
