@@ -55,7 +55,7 @@ def parse():
                    choices=["square", "rect", "grouped", "chain", "syr2k", "sweep"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
                         "grouped: 512 uneven problems; chain: Y = X W forward + backward; "
-                        "syr2k: the rank-2k update of Section 6.1 at N = K = --size; "
+                        "syr2k: the rank-2k update of Section 5.1 at N = K = --size; "
                         "sweep: sizes 1024..8192 x transposes x distributions x modes")
     return p.parse_args()
 
@@ -90,19 +90,83 @@ def load_peaks():
 
 
 # --------------------------------------------------------------- clocks
+_REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the
+    driver): SM clock, maximum SM clock, power draw and clock-event reasons
+    of one GPU, found by UUID.  Nothing is set."""
+
+    def __init__(self, uuid):
+        import ctypes
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if not uuid or self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev)) != 0:
+            raise OSError("no NVML handle for %s" % uuid)
+        v = ctypes.c_uint()
+        self.max_mhz = (float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(
+            self.dev, 1, ctypes.byref(v)) == 0 else None)
+
+    def sample(self):
+        ct = self.ct
+        mhz, mw, r = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        ok = self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(mhz)) == 0
+        pw = self.lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw)) == 0
+        rs = self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.dev, ct.byref(r)) == 0
+        return (float(mhz.value) if ok else None, mw.value / 1000.0 if pw else None,
+                int(r.value) if rs else 0)
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons (every 100 ms)."""
+    """SM clock, power and clock-event reasons DURING a timed region.
+
+    In-process NVML sampling every `period_s` (2 ms) on a background thread;
+    where NVML is unavailable, nvidia-smi at its 100 ms floor.  Every sample
+    is taken between start() (called just before the region's first launch)
+    and stop() (called after its final synchronise), while the GPU works
+    through the queued steps, so all samples count as under load."""
 
     FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, uuid):
+    def __init__(self, uuid, period_s=0.002):
         self.uuid = uuid
+        self.period = period_s
+        self.nvml = None
         self.proc = None
         self.path = None
+        self.thread = None
+        self.rows = []
+        try:
+            self.nvml = _Nvml(uuid)
+        except (OSError, AttributeError):
+            self.nvml = None
 
     def start(self):
+        self.rows = []
+        if self.nvml is not None:
+            import threading
+
+            self._stop = threading.Event()
+
+            def run():
+                while not self._stop.is_set():
+                    self.rows.append(self.nvml.sample())
+                    self._stop.wait(self.period)
+
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -115,6 +179,25 @@ class ClockSampler:
         time.sleep(0.25)
 
     def stop(self):
+        if self.nvml is not None and self.thread is not None:
+            self._stop.set()
+            self.thread.join()
+            self.thread = None
+            rows = self.rows
+            if not rows:
+                return None
+            mhz = [r[0] for r in rows if r[0] is not None]
+            watts = [r[1] for r in rows if r[1] is not None]
+            reasons = sorted({name for r in rows for bit, name in _REASON_BITS.items()
+                              if r[2] & bit})
+            return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                    "sm_mhz_min": min(mhz) if mhz else None,
+                    "sm_mhz_max": max(mhz) if mhz else None,
+                    "sm_max_mhz": self.nvml.max_mhz, "reasons": reasons,
+                    "power_w_median": statistics.median(watts) if watts else None,
+                    "power_w_max": max(watts) if watts else None,
+                    "samples": len(rows), "samples_under_load": len(rows),
+                    "source": "NVML in-process, every %g ms" % (1e3 * self.period)}
         if self.proc is None:
             return None
         time.sleep(0.15)
@@ -143,7 +226,25 @@ class ClockSampler:
         busy = [float(r[1]) for r in rows
                 if r[3].replace(".", "").isdigit() and float(r[3]) > 250.0] or mhz
         return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": maxmhz,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(busy),
+                "source": "nvidia-smi every 100 ms"}
+
+
+def median_ci(xs):
+    """Median of a sample with its distribution-free 95 % confidence interval:
+    the order statistics of (1-based) ranks floor(n/2 - 0.98 sqrt(n)) + 1 and
+    ceil(n/2 + 0.98 sqrt(n)), the normal approximation of the binomial count
+    of samples below the median (n = 20 gives ranks 6 and 15)."""
+    import math
+
+    x = sorted(xs)
+    n = len(x)
+    if n == 0:
+        return None
+    lo = max(0, int(math.floor(n / 2.0 - 0.98 * math.sqrt(n))))
+    hi = min(n - 1, int(math.ceil(n / 2.0 + 0.98 * math.sqrt(n))) - 1)
+    return {"median": statistics.median(x), "ci95": [x[lo], x[hi]], "mean": sum(x) / n,
+            "min": x[0], "max": x[-1], "n": n}
 
 
 # --------------------------------------------------------------- helpers
@@ -217,15 +318,15 @@ def time_steps(fn, steps, warmup, world, stream):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
         fn()
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    return e0.elapsed_time(e1)
+    time_steps.per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[steps])
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -335,55 +436,95 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    sampler.start()
-    h.lib.gemm_profile_enable(h.h, 1)
-    ms = time_steps(step, args.steps, 0, world, stream)
     import ctypes
 
-    main_ms, main_n = ctypes.c_double(), ctypes.c_int()
-    h.lib.gemm_profile_read(h.h, ctypes.byref(main_ms), ctypes.byref(main_n))
-    h.lib.gemm_profile_enable(h.h, 0)
+    h.lib.gemm_profile_enable(h.h, 1)
+    sampler.start()
+    ms = time_steps(step, args.steps, 0, world, stream)
     clocks = sampler.stop()
+    step_stats = median_ci(time_steps.per_step)
+    kern = (ctypes.c_float * args.steps)()
+    main_n = ctypes.c_int()
+    h.lib.gemm_profile_read_each(h.h, kern, args.steps, ctypes.byref(main_n))
+    h.lib.gemm_profile_enable(h.h, 0)
+    kern_stats = median_ci(list(kern)[:min(args.steps, main_n.value)])
     if h.sync() != 0:
         raise RuntimeError("kernel reported a bounded-wait timeout")
     ms_max = max_over_ranks(ms, world)
     flops = 2.0 * M * N * K
     value = replica_tflops(flops, args.steps, ms_max, world)
-    kernel_ms = main_ms.value / max(1, main_n.value)
+    kernel_ms = kern_stats["mean"] if kern_stats else float("nan")
 
     peaks, peak_src = load_peaks()
+    # A timed region under a second is a burst: the kernel is rated against
+    # the burst peak; a seconds-long region settles under the power cap and
+    # is rated against the sustained one.
+    region_s = ms / 1e3
+    sustained = region_s >= 1.0
+    sms = props.multi_processor_count
     if mode == "f32_simt":
-        sm = props.multi_processor_count
-        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": flops / (kernel_ms / 1e3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": "%d SMs x 128 FP32 lanes x 2 x max clock" % sm}
+                "unit": "TFLOP/s", "peak_source": "%d SMs x 128 FP32 lanes x 2 x max clock" % sms}
     else:
         tensor_flops = flops * (3 if mode == "bf16x3" else 1)
-        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        peak = peaks.get(key, peaks.get("bf16_tflops"))
         roof = {"bound": "tensor", "achieved": tensor_flops / (kernel_ms / 1e3) / 1e12,
                 "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "%s dense BF16 (cuBLAS, sustained)" % peak_src}
+                "peak_source": "%s dense BF16 (cuBLAS, %s): the timed region lasted %.3f s"
+                               % (peak_src, "sustained" if sustained else "burst", region_s)}
+        mhz = clocks.get("sm_mhz") if clocks else None
+        if mhz:
+            # tensor work per SM per clock at the clock the kernel ran at,
+            # against the dense rate of 4096 BF16 multiply-adds (8192 flops)
+            # per SM per clock (one 128 x 256 x 16 MMA every 128 cycles)
+            per_clk = tensor_flops / (kernel_ms / 1e3) / (mhz * 1e6) / sms
+            roof["per_clock"] = {"flop_per_clk_per_sm": per_clk, "frac_of_8192": per_clk / 8192.0,
+                                 "sm_mhz": mhz}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = load_traffic() if (mode == "bf16x3" and n == 8192) else None
     roof["kernel_ms"] = kernel_ms
+    roof["kernel_ms_stats"] = kern_stats
 
-    # FP32 SIMT comparison on the same workload
+    # FP32 SIMT comparison on the same workload: the two variants one call
+    # at a time in randomised order (each timed with its own events), then
+    # medians and 95 % intervals per variant
     compare = None
     if not args.no_compare and mode != "f32_simt":
-        simt_steps = max(3, min(10, args.steps))
+        import random
+
+        rounds = max(3, min(10, args.steps))
         h.ensure_workspace(h.workspace_size(g.MODES["f32_simt"], 0, 0, M, N, K))
         for _ in range(2):
             step(g.MODES["f32_simt"])
         torch.cuda.synchronize()
+        order = [mode, "f32_simt"] * rounds
+        random.Random(SEED).shuffle(order)
+        evs = []
         simt_clocks = ClockSampler(uuid)
         simt_clocks.start()
-        ms_s = time_steps(lambda: step(g.MODES["f32_simt"]), simt_steps, 0, world, stream)
+        for md in order:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(g.MODES[md])
+            e1.record(stream)
+            evs.append((md, e0, e1))
+        torch.cuda.synchronize()
         sclk = simt_clocks.stop()
-        ms_s = max_over_ranks(ms_s, world)
-        simt = world * flops * simt_steps / (ms_s / 1e3) / 1e12
-        sms = props.multi_processor_count
+        per = {mode: [], "f32_simt": []}
+        for md, e0, e1 in evs:
+            per[md].append(e0.elapsed_time(e1))
+        simt_stats = median_ci(per["f32_simt"])
+        ours_stats = median_ci(per[mode])
+        ms_s = max_over_ranks(simt_stats["median"], world)
+        simt = world * flops / (ms_s / 1e3) / 1e12
         compare = {"f32_simt_tflops": simt, "speedup_vs_f32_simt": value / simt,
-                   "f32_simt_ms_per_step": ms_s / simt_steps, "f32_simt_clocks": sclk}
+                   "f32_simt_ms_per_step": ms_s, "order": "randomised, %d calls each" % rounds,
+                   "f32_simt_ms_stats": simt_stats, "%s_ms_stats" % mode: ours_stats,
+                   "speedup_of_medians": simt_stats["median"] / ours_stats["median"],
+                   "clocks": sclk}
         if sclk and sclk.get("sm_mhz"):
             # FP32 peak at the clock the SIMT kernel actually ran at
             peak_at_clock = sms * 128 * 2 * sclk["sm_mhz"] * 1e6 / 1e12
@@ -416,6 +557,15 @@ def run_ours(args):
                "cores": threads, "kind": "oracle",
                "sample": "%d evenly spaced rows of C (all %d columns, K=%d), FP64 triple loop"
                          % (len(rows), N, K)}
+        # the same oracle on one thread (a few rows, about a second)
+        import oracle
+
+        one = rows[:: max(1, len(rows) // 8)][:8]
+        t0 = time.perf_counter()
+        oracle.gemm(A, B, ALPHA, BETA, C0, rows=one, threads=1)
+        el1 = time.perf_counter() - t0
+        cpu["single_thread"] = {"value": 2.0 * len(one) * N * K / el1 / 1e12, "cores": 1,
+                                "sample": "%d of the same rows" % len(one)}
         import oracle
 
         errs = {}
@@ -436,6 +586,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": square_config(n, mode, world, args.operand_layout),
         "launches_per_step": launches_per_step,
+        "step_ms_stats": step_stats,
         "roofline": roof,
         "gpu_launches": launches_per_step * args.steps,
         "e2e": e2e,
@@ -473,7 +624,8 @@ def _events_ms(fn, steps, warmup, stream):
 
 def run_rect(args):
     """BF16-input rectangular/skinny GEMMs (FP32 accumulate and output),
-    entries N(0, 1/sqrt(K)), alpha = 1, beta = 0, through gemm_bf16."""
+    entries N(0, 1/sqrt(K)), alpha = 1, beta = 0, through gemm_bf16; and the
+    3xBF16 mode through gemm() on FP32 copies of the same inputs."""
     import numpy as np
     import torch
 
@@ -503,12 +655,33 @@ def run_rect(args):
                            args.warmup, stream)
         flops = 2.0 * M * N * K
         nbytes = 2.0 * (M * K + N * K) + 4.0 * M * N
-        out.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
-                    "gbs": nbytes / ms / 1e6,
-                    "frac_tensor": flops / ms / 1e9 / peaks["bf16_tflops"],
-                    "frac_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"],
-                    "launches": launches, "nt_ms": ms_nt})
-        del A, B, Bt, C
+        row = {"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
+               "gbs": nbytes / ms / 1e6,
+               "frac_tensor": flops / ms / 1e9 / peaks["bf16_tflops"],
+               "frac_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"],
+               "launches": launches, "nt_ms": ms_nt}
+        # the 3xBF16 leg: the same values as FP32 copies through gemm()
+        # (split precision on FP32 operands); its bytes are the FP32 inputs
+        # and the FP32 output, and sampled rows give its error
+        A32, B32 = A.float(), B.float()
+        ms3 = _events_ms(lambda: g.matmul(A32, B32, C=C, mode="bf16x3", h=h), args.steps,
+                         args.warmup, stream)
+        launches3 = h.last_launch_count()
+        nbytes3 = 4.0 * (M * K + N * K + M * N)
+        rows = np.linspace(0, M - 1, 4).astype(np.int64)
+        g.matmul(A32, B32, C=C, mode="bf16x3", h=h)
+        torch.cuda.synchronize()
+        import oracle
+
+        C64, D, _ = oracle.gemm(A32.cpu().numpy(), B32.cpu().numpy(), rows=rows)
+        row["bf16x3"] = {"ms": ms3, "tflops": flops / ms3 / 1e9, "gbs": nbytes3 / ms3 / 1e6,
+                         "frac_hbm": nbytes3 / ms3 / 1e6 / peaks["hbm_gbs"],
+                         "frac_tensor_div3": 3 * flops / ms3 / 1e9 / peaks["bf16_tflops"],
+                         "launches": launches3,
+                         "normwise_error": oracle.normwise_error(C[torch.from_numpy(rows).cuda()]
+                                                                 .cpu().numpy(), C64, D)}
+        out.append(row)
+        del A, B, Bt, C, A32, B32
     h.close()
     tot_flops = sum(2.0 * r["M"] * r["N"] * r["K"] for r in out)
     tot_ms = sum(r["ms"] for r in out)
@@ -605,7 +778,7 @@ def run_chain(args):
 
 
 def run_syr2k(args):
-    """SYR2K (Section 6.1): lower triangle of C <- 1.5 (A B^T + B A^T) + 0.5 C,
+    """SYR2K (Section 5.1): lower triangle of C <- 1.5 (A B^T + B A^T) + 0.5 C,
     A, B FP32 N x K U[-1, 1], N = K = --size; the chosen mode against the
     FP32 SIMT variant, sampled rows against the FP64 oracle."""
     import ctypes

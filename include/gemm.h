@@ -293,7 +293,7 @@ gemm_status_t gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
 /* Triangle selector of gemm_syr2k (diagonal included in both). */
 typedef enum { GEMM_LOWER = 0, GEMM_UPPER = 1 } gemm_uplo_t;
 
-/* SYR2K, the rank-2k update of Section 6.1 ("macro-level strategy for other
+/* SYR2K, the rank-2k update of Section 5.1 ("macro-level strategy for other
  * BLAS kernels"): on the `uplo` triangle of the N x N matrix C,
  *   trans == GEMM_OP_N: C <- alpha (A B^T + B A^T) + beta C, A and B N x K;
  *   trans == GEMM_OP_T: C <- alpha (A^T B + B^T A) + beta C, A and B K x N;
@@ -343,27 +343,48 @@ gemm_status_t gemm_profile_enable(gemm_handle_t handle, int enable);
  * their number; then forget them. */
 gemm_status_t gemm_profile_read(gemm_handle_t handle, double *main_ms, int *main_launches);
 
+/* The same events one launch at a time: writes the duration (milliseconds)
+ * of each recorded main kernel, in launch order, to ms[0 .. capacity-1],
+ * sets *count to the number recorded (which may exceed capacity; the rest
+ * are dropped), then forgets them.  Positions: 1 handle, 2 ms (NULL with
+ * capacity > 0), 3 capacity (< 0), 4 count.  Not in the paper. */
+gemm_status_t gemm_profile_read_each(gemm_handle_t handle, float *ms, int capacity, int *count);
+
 /* gemm() in GEMM_MODE_BF16X3 for callers that cannot allocate device
- * memory (code running where cudaMalloc is forbidden or would stall, such as
- * host callbacks, allocator hooks, or plugins whose host owns all device
- * memory).  No handle: it calls no cudaMalloc, cudaFree or other allocating
- * routine.  The paper has no counterpart.
- * Scratch is one 64 MiB device array inside the library, reserved on every
- * GPU that loads the library until the process exits; a problem must fit:
- * 4 * (M + N) * round_up(K, 8) bytes <= 64 MiB, else GEMM_ERR_WORKSPACE and
- * nothing is launched.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make it
- * before any stream capture.  All calls share the array (it keeps the last
- * call's contents; each call overwrites what it reads): calls whose GPU
- * work overlaps, on different streams or threads, race -- serialise them.
- * Invalid arguments give GEMM_ERR_ARG (no position is recorded: there is no
- * handle); a bounded-wait expiry is not reported.  Same arguments and
- * results as gemm() in GEMM_MODE_BF16X3 without split-K. */
+ * memory: code running where cudaMalloc is forbidden or would stall, such as
+ * a custom allocator's own hooks, a plugin whose host application owns all
+ * device memory, or a loop that must never enter the driver's allocator.
+ * No handle: it calls no cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart.
+ * Scratch is one 64 MiB device array inside the library.  The runtime
+ * reserves it on a GPU when it loads the library's module there -- with
+ * lazy module loading (the CUDA default) during the FIRST call on that
+ * device, which is also when the call looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current.  That first call may
+ * therefore synchronise or fail for lack of memory: make it once at
+ * start-up, before any stream capture.  The array is kept until the process
+ * exits.  A problem must fit: 4 * (M + N) * round_up(K, 8) bytes <= 64 MiB,
+ * else GEMM_ERR_WORKSPACE and nothing is launched.  All calls share the
+ * array (it keeps the last call's contents; each call overwrites what it
+ * reads): calls whose GPU work overlaps, on different streams or threads,
+ * race -- serialise them.  Invalid arguments give GEMM_ERR_ARG (no position
+ * is recorded: there is no handle).  A kernel that abandons a bounded wait
+ * leaves C undefined and sets a device error word that
+ * gemm_bf16x3_noalloc_check reports.  Same arguments and results as gemm()
+ * in GEMM_MODE_BF16X3 without split-K. */
 gemm_status_t gemm_bf16x3_noalloc(gemm_op_t transA, gemm_op_t transB,
                                   int64_t M, int64_t N, int64_t K,
                                   float alpha, const float *A, int64_t lda,
                                   const float *B, int64_t ldb,
                                   float beta, float *C, int64_t ldc, void *stream);
+
+/* Synchronise `stream`, then read and clear gemm_bf16x3_noalloc's device
+ * error word on the current device: GEMM_ERR_TIMEOUT if a call since the
+ * last check abandoned a bounded wait (its C is undefined), GEMM_ERR_CUDA if
+ * the stream reported an error, GEMM_ERR_DEVICE if the current device is
+ * not an sm_103 GPU, else GEMM_OK.  Allocates nothing.  The paper has no
+ * counterpart. */
+gemm_status_t gemm_bf16x3_noalloc_check(void *stream);
 
 /* Synchronise `stream`, then read and clear the handle's device error word:
  * GEMM_ERR_TIMEOUT if a kernel abandoned a bounded wait since the last

@@ -14,7 +14,7 @@ loop nest computes alpha * op(A) op(B) + beta * C with beta applied once):
   ``gemm_ref.c``).
 * ``split_bf16`` / ``bf16_bits_to_f32`` -- the hi/lo BF16 split.
 * ``syr2k`` -- one triangle of C = alpha (opA opB^T + opB opA^T) + beta C,
-  the rank-2k update of Section 6.1 (exact or with split products).
+  the rank-2k update of Section 5.1 (exact or with split products).
 * ``normwise_error`` -- max |C - C64| / max D, the error measure.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` (the checks in

@@ -31,7 +31,7 @@
  * rounding the dropped 16 bits to nearest with ties to even; for
  * non-finite hi, lo = 0.
  *
- * The file also holds the SYR2K update of Section 6.1 (oracle_syr2k, at
+ * The file also holds the SYR2K update of Section 5.1 (oracle_syr2k, at
  * the end), written out from its definition in the same way.
  *
  * Parity of every function here is pinned by the CPU tests against brute
@@ -238,7 +238,7 @@ int oracle_gemm_split_terms(int transA, int transB, int64_t M, int64_t N, int64_
 }
 
 /*
- * SYR2K, the rank-2k update used as the example of Section 6.1 (macro-level
+ * SYR2K, the rank-2k update used as the example of Section 5.1 (macro-level
  * strategy for other BLAS kernels): one triangle of the symmetric C,
  *
  *   C64[i][j] = alpha * sum_p ( opA[i][p] opB[j][p] + opB[i][p] opA[j][p] )
@@ -248,7 +248,7 @@ int oracle_gemm_split_terms(int transA, int transB, int64_t M, int64_t N, int64_
  * (upper), diagonal included -- where opX is X (stored N x K, trans == 0)
  * or X^T (X stored K x N, trans == 1).  That is C <- alpha (A B^T + B A^T)
  * + beta C, or alpha (A^T B + B^T A) + beta C, the two GEMM updates of each
- * block that Section 6.1 describes.  Both products of one p are summed
+ * block that Section 5.1 describes.  Both products of one p are summed
  * first and then accumulated in increasing p, so C64[i][j] of the lower
  * triangle equals C64[j][i] of the upper one bit for bit.
  *

@@ -78,8 +78,11 @@ _SIGS = {
     "gemm_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "gemm_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int)]),
+    "gemm_profile_read_each": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]),
     "gemm_bf16x3_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _f32,
                                            _vp, _i64, _vp, _i64, _f32, _vp, _i64, _vp]),
+    "gemm_bf16x3_noalloc_check": (ctypes.c_int, [_vp]),
     "gemm_sync": (ctypes.c_int, [_vp, _vp]),
     "gemm_last_error_arg": (ctypes.c_int, [_vp]),
     "gemm_get_last_error_arg": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),

@@ -83,11 +83,13 @@ bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
 }
 
 // Tile plan of one tensor-core launch.  Library choice (configuration 0):
-//  * split precision on split operands: CTA pairs (256 x 256 tiles,
-//    cta_group::2, BK 64) when there are at least as many pair tiles as SM
-//    pairs, since each SM then stages half of B and runs ~12 % fewer cycles
-//    per GEMM; one CTA per 128 x 256 tile (BK 32) otherwise.  Plain BF16 runs
-//    one CTA per tile (BK 64), which measured faster than pairs;
+//  * CTA pairs (256 x 256 tiles, cta_group::2, BK 64) when there are at
+//    least as many pair tiles as SM pairs, for split precision on split
+//    operands (each SM then stages half of B and runs ~12 % fewer cycles per
+//    GEMM) and for plain BF16 with K >= 512 (7-14 % faster than one CTA per
+//    tile from K = 1024 up, with a second producer warp for the B copies);
+//    one CTA per 128 x 256 tile otherwise (BK 32 for split precision, 64
+//    for plain BF16);
 //  * operands K-major for split operands (the split transposes at nearly the
 //    copy rate and the K-major kernel runs a few % faster) and for gemm_bf16
 //    when packing pays (pack_pays); in their stored orientation otherwise,
@@ -974,6 +976,30 @@ gemm_status_t gemm_profile_read(gemm_handle_t h, double* main_ms, int* main_laun
     h->ev_used = 0;
     *main_ms = total;
     *main_launches = n;
+    return GEMM_OK;
+}
+
+gemm_status_t gemm_profile_read_each(gemm_handle_t h, float* ms, int capacity, int* count) {
+    if (!h) return fail_arg(h, 1);
+    if (!ms && capacity > 0) return fail_arg(h, 2);
+    if (capacity < 0) return fail_arg(h, 3);
+    if (!count) return fail_arg(h, 4);
+    int n = 0;
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        if (cudaEventSynchronize(h->ev_pool[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return GEMM_ERR_CUDA;
+        }
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return GEMM_ERR_CUDA;
+        }
+        if (n < capacity) ms[n] = t;
+        ++n;
+    }
+    h->ev_used = 0;
+    *count = n;
     return GEMM_OK;
 }
 

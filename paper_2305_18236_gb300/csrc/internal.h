@@ -94,7 +94,7 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
                    const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
                    int* launches);
 
-// SYR2K (Section 6.1) on the tensor cores: the `uplo` (1 lower, 2 upper)
+// SYR2K (Section 5.1) on the tensor cores: the `uplo` (1 lower, 2 upper)
 // triangle of C (N x N) <- alpha (X Y^T + Y X^T) + beta C, X and Y the two
 // N x K operands stored in one buffer `xy`: planes [0, P) hold X, planes
 // [P, 2P) hold Y (P = 1 for nterms 1: hi; 2 for nterms 3: hi, lo), with

@@ -1,30 +1,37 @@
 // gemm_bf16x3_noalloc: the split-precision GEMM for callers that cannot
 // allocate device memory.
 //
-// Who needs this: code that runs where cudaMalloc is off limits -- for
-// example inside a host callback or a custom allocator's own hooks, in a
-// plugin whose host application owns all device memory and forbids other
-// allocations, or in a latency-critical loop that must never hit the
-// driver's allocator (which can synchronise the device).  gemm() needs a
-// handle, and both the handle and its workspace come from cudaMalloc; this
-// entry point needs neither.
+// Who needs this: code that runs where cudaMalloc is off limits -- a custom
+// allocator's own hooks (which must not re-enter the allocator), a plugin
+// whose host application owns all device memory and forbids other
+// allocations, or a latency-critical loop that must never hit the driver's
+// allocator (which can synchronise the device).  gemm() needs a handle, and
+// both the handle and its workspace come from cudaMalloc; this entry point
+// needs neither.
 //
 // Its scratch (the BF16 hi/lo copies of op(A) and op(B), i.e. the packed
 // operands the tensor-core kernel reads) lives in one file-scope device array
-// of kScratchBytes = 64 MiB that the CUDA runtime reserves when the library's
-// module is loaded on a GPU and keeps until the process exits.  Nothing here
-// calls cudaMalloc, cudaFree or any allocating library routine.
+// of kScratchBytes = 64 MiB.  The CUDA runtime reserves it when it loads this
+// file's module on a GPU and keeps it until the process exits.  With lazy
+// module loading (the default since CUDA 12.2) that load happens during the
+// first call on each device -- the address lookup below triggers it -- so
+// that first call is the one that reserves the 64 MiB and may synchronise or
+// fail for lack of memory: make it once at start-up, before any stream
+// capture.  Nothing here calls cudaMalloc, cudaFree or any allocating
+// library routine.
 //
 // Host code cannot use the array's name as a device address (on the host it
-// names a stand-in object), so the first call on each device -- with that
-// device current -- asks the runtime for the array's device address with
-// cudaGetSymbolAddress and caches it.  Make that first call before any
-// stream capture begins.
+// names a stand-in object), so each device's first call -- with that device
+// current -- asks the runtime for the array's device address with
+// cudaGetSymbolAddress and caches it; a failed lookup is not cached and is
+// retried by the next call.
 //
 // All calls share the one array and it keeps whatever the last call wrote:
-// every call overwrites the parts it reads, and clears the small error word
-// it owns before launching.  Calls whose GPU work can overlap (different
-// streams, or different host threads) race on the array; serialise them.
+// every call overwrites the parts it reads.  A separate device error word
+// collects bounded-wait expiries of every call until
+// gemm_bf16x3_noalloc_check reads and clears it.  Calls whose GPU work can
+// overlap (different streams, or different host threads) race on the array;
+// serialise them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,17 +47,53 @@ constexpr size_t kScratchBytes = size_t(64) << 20;
 constexpr int kMaxDevices = 64;
 
 // The scratch array itself, and a separate error word for the kernels'
-// bounded waits (cleared at the start of every call).
+// bounded waits (zero at module load; cleared by gemm_bf16x3_noalloc_check).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 static __device__ __align__(256) int g_noalloc_err[64];
 
 struct DeviceAddrs {
-    std::once_flag once;
-    cudaError_t rc = cudaSuccess;
+    bool ready = false;  // set only after both lookups succeeded
     unsigned char* scratch = nullptr;
     int* err = nullptr;
 };
 DeviceAddrs g_addrs[kMaxDevices];
+std::mutex g_addrs_mu;
+
+// The device addresses of the scratch array and the error word on the
+// current device `dev` (looked up once; a failure is retried next time).
+cudaError_t device_addrs(int dev, DeviceAddrs** out) {
+    std::lock_guard<std::mutex> lock(g_addrs_mu);
+    DeviceAddrs& d = g_addrs[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        void* e = nullptr;
+        cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (rc == cudaSuccess) rc = cudaGetSymbolAddress(&e, g_noalloc_err);
+        if (rc != cudaSuccess) {
+            cudaGetLastError();
+            return rc;
+        }
+        d.scratch = static_cast<unsigned char*>(p);
+        d.err = static_cast<int*>(e);
+        d.ready = true;
+    }
+    *out = &d;
+    return cudaSuccess;
+}
+
+// Current device, checked to be an sm_103 GPU within the address table.
+gemm_status_t current_device(int* dev, int* sms) {
+    if (cudaGetDevice(dev) != cudaSuccess || *dev < 0 || *dev >= kMaxDevices) {
+        cudaGetLastError();
+        return GEMM_ERR_DEVICE;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, *dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, *dev);
+    cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *dev);
+    if (major != 10 || minor != 3) return GEMM_ERR_DEVICE;
+    return GEMM_OK;
+}
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -84,33 +127,13 @@ extern "C" gemm_status_t gemm_bf16x3_noalloc(gemm_op_t transA, gemm_op_t transB,
         a_bytes + b_bytes > kScratchBytes)
         return GEMM_ERR_WORKSPACE;  // 4 * (M + N) * round_up(K, 8) bytes must fit in 64 MiB
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return GEMM_ERR_DEVICE;
-    }
-    int major = 0, minor = 0, sms = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (major != 10 || minor != 3) return GEMM_ERR_DEVICE;
+    int dev = 0, sms = 0;
+    const gemm_status_t dst = current_device(&dev, &sms);
+    if (dst != GEMM_OK) return dst;
+    DeviceAddrs* dp = nullptr;
+    if (device_addrs(dev, &dp) != cudaSuccess) return GEMM_ERR_CUDA;
+    DeviceAddrs& d = *dp;
 
-    // Once per device, with that device current: the arrays' device addresses.
-    DeviceAddrs& d = g_addrs[dev];
-    std::call_once(d.once, [&d] {
-        void* p = nullptr;
-        d.rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (d.rc == cudaSuccess) d.scratch = static_cast<unsigned char*>(p);
-        void* e = nullptr;
-        if (d.rc == cudaSuccess) d.rc = cudaGetSymbolAddress(&e, g_noalloc_err);
-        if (d.rc == cudaSuccess) d.err = static_cast<int*>(e);
-    });
-    if (d.rc != cudaSuccess || !d.scratch || !d.err) {
-        cudaGetLastError();
-        return GEMM_ERR_CUDA;
-    }
-
-    if (cudaMemsetAsync(d.err, 0, sizeof(int), s) != cudaSuccess) return GEMM_ERR_CUDA;
     uint16_t* a_hi = reinterpret_cast<uint16_t*>(d.scratch);
     uint16_t* b_hi = reinterpret_cast<uint16_t*>(d.scratch + a_bytes);
     const int64_t a_plane = M * kp, b_plane = N * kp;
@@ -127,4 +150,25 @@ extern "C" gemm_status_t gemm_bf16x3_noalloc(gemm_op_t transA, gemm_op_t transB,
     const int rc = gb300::launch_tc_gemm(oa, ob, 3, M, N, K, alpha, beta, C, ldc, nullptr, cfg,
                                          d.err, sms, s, &launches);
     return rc == 0 ? GEMM_OK : static_cast<gemm_status_t>(rc);
+}
+
+extern "C" gemm_status_t gemm_bf16x3_noalloc_check(void* stream) {
+    int dev = 0, sms = 0;
+    const gemm_status_t dst = current_device(&dev, &sms);
+    if (dst != GEMM_OK) return dst;
+    DeviceAddrs* d = nullptr;
+    if (device_addrs(dev, &d) != cudaSuccess) return GEMM_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_CUDA;
+    }
+    int word = 0;
+    if (cudaMemcpyAsync(&word, d->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(d->err, 0, sizeof(int), s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return GEMM_ERR_CUDA;
+    }
+    return word != 0 ? GEMM_ERR_TIMEOUT : GEMM_OK;
 }

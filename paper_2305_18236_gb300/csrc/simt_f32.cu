@@ -7,14 +7,18 @@
 //    a BK = 16 slice of K plays kc;
 //  * the shared-memory tiles As[k][m], Bs[k][n] are the packed ATile/BTile
 //    buffers (Section 3.1: tiles stored in the order the micro kernel reads
-//    them), double-buffered with a register prefetch of the next K slice;
+//    them).  When both operands are stored K x rows (the form the library
+//    packs large problems into) a three-stage ring filled by cp.async
+//    copies stages them with no registers in flight; the other orientations
+//    double-buffer them with a register prefetch of the next K slice;
 //  * each thread's 8 x 8 register accumulator is the mr x nr micro tile of
-//    Algorithm 2, updated by rank-1 outer products and never spilled;
+//    Algorithm 2, updated by rank-1 outer products (Blackwell's packed FP32
+//    FMA, two fused multiply-adds per instruction) and never spilled;
 //  * remainder tiles are zero-filled on load and stored element by element
 //    (Section 3.1, last paragraph), full tiles with 16-byte accesses.
 // All four op(A)/op(B) combinations are handled by the load index math.
 //
-// SYR2K (Section 6.1, UPLO 1 = lower / 2 = upper triangle): the same kernel
+// SYR2K (Section 5.1, UPLO 1 = lower / 2 = upper triangle): the same kernel
 // over the two GEMM updates of each C block.  The K loop runs over both
 // products, A-side rows of X with B-side rows of Y and then the reverse, each
 // half zero-padded to whole BK slices; blocks wholly outside the triangle

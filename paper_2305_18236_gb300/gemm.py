@@ -170,7 +170,7 @@ def matmul(A, B, C=None, alpha=1.0, beta=0.0, transA=False, transB=False, mode="
 
 
 def syr2k(A, B, C=None, alpha=1.0, beta=0.0, uplo="lower", trans=False, mode="bf16x3", h=None):
-    """SYR2K (Section 6.1): the ``uplo`` triangle of C <- alpha (A B^T + B A^T)
+    """SYR2K (Section 5.1): the ``uplo`` triangle of C <- alpha (A B^T + B A^T)
     + beta C for float32 CUDA tensors A, B of shape (N, K), or alpha (A^T B +
     B^T A) + beta C for shape (K, N) with ``trans``.  The other triangle of C
     is left as it is (uninitialised when C is None)."""

@@ -324,7 +324,7 @@ def check_split_terms_reduce(orc):
 
 
 # ------------------------------------------------------------------ SYR2K
-# Section 6.1: one triangle of C <- alpha (opA opB^T + opB opA^T) + beta C,
+# Section 5.1: one triangle of C <- alpha (opA opB^T + opB opA^T) + beta C,
 # opX = X (stored N x K) or X^T (stored K x N); the other triangle is not
 # part of the update.
 

@@ -314,6 +314,44 @@ def test_headline_size_sampled(mode, dist):
     check_mode(mode, A, B, 1.5, 0.5, C0, False, False, rows=rows, tol=tol)
 
 
+@pytest.mark.parametrize("dist", ["uniform", "log_uniform"])
+@pytest.mark.parametrize("tA,tB", [(False, False), (False, True), (True, False), (True, True)])
+@pytest.mark.parametrize("n", [2048, 4096, 8192])
+def test_square_sizes_all_transposes_sampled(n, tA, tB, dist):
+    """The square sizes 2048, 4096 and 8192 in every orientation (Algorithm
+    1's op(A) / op(B) access order), alpha = 1.5, beta = 0.5, 3xBF16 in the
+    library's launch configuration: 16 sampled rows against both oracles
+    (the exact GEMM at the mode's bound, and the GEMM of the same BF16 split
+    products at the accumulation bound).  Uniform data at 8192 must reach
+    the 1e-6 normwise bar in every orientation."""
+    A, B, C0 = make_problem(n, n, n, transA=tA, transB=tB, seed=0x5EED + n, dist=dist, beta=0.5)
+    rows = np.linspace(0, n - 1, 16).astype(np.int64)
+    tol = 1e-6 if (n == 8192 and dist == "uniform") else None
+    check_mode("bf16x3", A, B, 1.5, 0.5, C0, tA, tB, rows=rows, tol=tol)
+
+
+@pytest.mark.parametrize("tA,tB", [(False, True), (True, False), (True, True)])
+def test_headline_size_f32_simt_other_transposes(tA, tB):
+    """The FP32 SIMT comparison arm at 8192 in the three other orientations
+    (FP32 fused multiply-adds: normwise 1e-6)."""
+    n = 8192
+    A, B, C0 = make_problem(n, n, n, transA=tA, transB=tB, seed=0x5EED, beta=0.5)
+    rows = np.linspace(0, n - 1, 16).astype(np.int64)
+    check_mode("f32_simt", A, B, 1.5, 0.5, C0, tA, tB, rows=rows)
+
+
+@pytest.mark.parametrize("M,N,K", [(16384, 4096, 1024), (4096, 16384, 4096), (128, 8192, 8192),
+                                   (8192, 8192, 64)])
+def test_rectangular_bf16x3_on_fp32_copies_sampled(M, N, K):
+    """The rectangular/skinny shapes in the 3xBF16 mode on FP32 copies of
+    BF16-valued normal(0, 1/sqrt(K)) inputs, through gemm(), on sampled rows:
+    exact GEMM and split-product GEMM bounds."""
+    A32, _ = inputs.bf16_values(inputs.normal((M, K), 121, 1 / np.sqrt(K)))
+    B32, _ = inputs.bf16_values(inputs.normal((K, N), 122, 1 / np.sqrt(K)))
+    rows = np.linspace(0, M - 1, 12).astype(np.int64)
+    check_mode("bf16x3", A32, B32, 1.0, 0.0, None, False, False, rows=rows)
+
+
 @pytest.mark.parametrize("M,N,K", [(16384, 4096, 1024), (4096, 16384, 4096), (128, 8192, 8192),
                                    (8192, 8192, 64)])
 def test_rectangular_bf16_sampled(M, N, K):

@@ -1,4 +1,4 @@
-"""SYR2K (Section 6.1) through the C ABI against the FP64 oracle (GB300 only).
+"""SYR2K (Section 5.1) through the C ABI against the FP64 oracle (GB300 only).
 
 C <- alpha (A B^T + B A^T) + beta C on one triangle (or alpha (A^T B + B^T A)
 + beta C with trans), every mode.  Elements outside the triangle must come

@@ -53,7 +53,7 @@ MUTANTS = {
     "rows_ignored": ("int64_t i = rows ? rows[r] : r;\n            for (int64_t j = 0; j < N; ++j) {\n                acc[j] = 0.0;\n                mag[j] = 0.0;",
                      "int64_t i = r;\n            for (int64_t j = 0; j < N; ++j) {\n                acc[j] = 0.0;\n                mag[j] = 0.0;"),
     "beta_read_when_zero": ("if (beta != 0.0) {\n                    double c0", "if (1) {\n                    double c0"),
-    # SYR2K (Section 6.1)
+    # SYR2K (Section 5.1)
     "syr2k_second_product_dropped": ("acc += aip * bjp + bip * ajp;", "acc += aip * bjp;"),
     "syr2k_wrong_operand": ("acc += aip * bjp + bip * ajp;", "acc += aip * bjp + aip * ajp;"),
     "syr2k_diagonal_excluded": ("int inside = uplo == 0 ? (j <= i) : (j >= i);",
