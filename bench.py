@@ -19,6 +19,7 @@ holds the FP32 SIMT kernel's throughput on the same workload.
     python bench.py --impl reference     # the CPU oracle arm
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -51,6 +52,9 @@ def parse():
                    help="auto: library choice; as_stored: operands stored K x rows are split "
                         "without transposing and read as MN-major tiles; k_major: every operand "
                         "made K-contiguous first")
+    p.add_argument("--split-place", default="auto", choices=["auto", "prepass", "in_kernel"],
+                   help="3xBF16: where FP32 operands are split into hi/lo BF16 -- library "
+                        "choice, a split pass before the kernel, or inside the kernel")
     p.add_argument("--workload", default="square",
                    choices=["square", "rect", "grouped", "chain", "syr2k", "sweep"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
@@ -100,8 +104,6 @@ class _Nvml:
     of one GPU, found by UUID.  Nothing is set."""
 
     def __init__(self, uuid):
-        import ctypes
-
         self.ct = ctypes
         self.lib = ctypes.CDLL("libnvidia-ml.so.1")
         if self.lib.nvmlInit_v2() != 0:
@@ -113,14 +115,30 @@ class _Nvml:
         self.max_mhz = (float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(
             self.dev, 1, ctypes.byref(v)) == 0 else None)
 
+    class _Field(ctypes.Structure):
+        # nvmlFieldValue_t: field id, scope id, timestamp, latency, value
+        # type, return code, 8-byte value union
+        _fields_ = [("fieldId", ctypes.c_uint), ("scopeId", ctypes.c_uint),
+                    ("timestamp", ctypes.c_longlong), ("latencyUsec", ctypes.c_longlong),
+                    ("valueType", ctypes.c_int), ("nvmlReturn", ctypes.c_int),
+                    ("value", ctypes.c_ulonglong)]
+
+    POWER_INSTANT = 186  # NVML_FI_DEV_POWER_INSTANT (milliwatts, unsigned int)
+
     def sample(self):
         ct = self.ct
-        mhz, mw, r = ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        mhz, r = ct.c_uint(), ct.c_ulonglong()
         ok = self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ct.byref(mhz)) == 0
-        pw = self.lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw)) == 0
         rs = self.lib.nvmlDeviceGetCurrentClocksEventReasons(self.dev, ct.byref(r)) == 0
-        return (float(mhz.value) if ok else None, mw.value / 1000.0 if pw else None,
-                int(r.value) if rs else 0)
+        f = self._Field(fieldId=self.POWER_INSTANT)
+        watts = None
+        if self.lib.nvmlDeviceGetFieldValues(self.dev, 1, ct.byref(f)) == 0 and f.nvmlReturn == 0:
+            watts = (f.value & 0xFFFFFFFF) / 1000.0
+        else:
+            mw = ct.c_uint()
+            if self.lib.nvmlDeviceGetPowerUsage(self.dev, ct.byref(mw)) == 0:
+                watts = mw.value / 1000.0
+        return (float(mhz.value) if ok else None, watts, int(r.value) if rs else 0)
 
     def close(self):
         self.lib.nvmlShutdown()
@@ -290,7 +308,7 @@ def replica_tflops(flops_per_step, steps, ms_max, world):
     return world * flops_per_step * steps / (ms_max / 1e3) / 1e12
 
 
-def square_config(n, mode, world, layout=None):
+def square_config(n, mode, world, layout=None, split_place=None):
     """The workload description shared by both arms of the headline line."""
     cfg = {"workload": "sgemm %dx%dx%d NN alpha=1.5 beta=0.5, A,B,C0 U[-1,1] seeded"
                        % (n, n, n),
@@ -298,6 +316,8 @@ def square_config(n, mode, world, layout=None):
            "l2": "inputs larger than L2 (A, B, C 268 MB each); no flush"}
     if layout is not None:
         cfg["operand_layout"] = layout
+    if split_place is not None:
+        cfg["split_place"] = split_place
     return cfg
 
 
@@ -385,7 +405,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": square_config(n, args.mode, world, args.operand_layout),
+        "config": square_config(n, args.mode, world, args.operand_layout, args.split_place),
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -415,7 +435,7 @@ def run_ours(args):
     dB = torch.from_numpy(B).to(dev)
     dC = torch.from_numpy(C0).to(dev)
     h = g.Gemm(dev)
-    h.set_config(operand_layout=args.operand_layout)
+    h.set_config(operand_layout=args.operand_layout, split_place=args.split_place)
     stream = torch.cuda.current_stream(dev)
     mode = args.mode
     mcode = g.MODES[mode]
@@ -436,7 +456,6 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    import ctypes
 
     h.lib.gemm_profile_enable(h.h, 1)
     sampler.start()
@@ -584,7 +603,7 @@ def run_ours(args):
         "dtype": {"bf16x3": "bf16x3 (bf16 hi/lo products, f32 accumulate)",
                   "bf16": "bf16 (f32 accumulate)", "f32_simt": "f32"}[mode],
         "data": "synthetic",
-        "config": square_config(n, mode, world, args.operand_layout),
+        "config": square_config(n, mode, world, args.operand_layout, args.split_place),
         "launches_per_step": launches_per_step,
         "step_ms_stats": step_stats,
         "roofline": roof,
@@ -667,6 +686,13 @@ def run_rect(args):
         ms3 = _events_ms(lambda: g.matmul(A32, B32, C=C, mode="bf16x3", h=h), args.steps,
                          args.warmup, stream)
         launches3 = h.last_launch_count()
+        places = {}
+        for place in ("prepass", "in_kernel"):
+            hx = g.Gemm()
+            hx.set_config(split_place=place)
+            places[place] = _events_ms(lambda: g.matmul(A32, B32, C=C, mode="bf16x3", h=hx),
+                                       args.steps, args.warmup, stream)
+            hx.close()
         nbytes3 = 4.0 * (M * K + N * K + M * N)
         rows = np.linspace(0, M - 1, 4).astype(np.int64)
         g.matmul(A32, B32, C=C, mode="bf16x3", h=h)
@@ -678,6 +704,7 @@ def run_rect(args):
                          "frac_hbm": nbytes3 / ms3 / 1e6 / peaks["hbm_gbs"],
                          "frac_tensor_div3": 3 * flops / ms3 / 1e9 / peaks["bf16_tflops"],
                          "launches": launches3,
+                         "ms_by_split_place": places,
                          "normwise_error": oracle.normwise_error(C[torch.from_numpy(rows).cuda()]
                                                                  .cpu().numpy(), C64, D)}
         out.append(row)
@@ -696,8 +723,9 @@ def run_rect(args):
 
 def run_grouped(args):
     """512 problems, M, N, K uniform multiples of 32 in [64, 2048], FP32,
-    3xBF16, alpha = 1, beta = 0: autotuned + graph-captured plan vs the fixed
-    default configuration (eager)."""
+    3xBF16, alpha = 1, beta = 0: the library's plan (cost model) eager and
+    graph-captured, one CTA per tile, the split pass or the in-kernel split
+    forced, and the autotuned plan."""
     import numpy as np
     import torch
 
@@ -723,8 +751,14 @@ def run_grouped(args):
     with torch.cuda.stream(stream):
         hp = g.Gemm()
         hp.set_config(operand_layout=args.operand_layout, cta_group=1)
+        hf = g.Gemm()
+        hf.set_config(operand_layout=args.operand_layout, split_place="in_kernel")
+        hs = g.Gemm()
+        hs.set_config(operand_layout=args.operand_layout, split_place="prepass")
         for name, kw, hh in [("model_eager", dict(), h), ("model_graph", dict(graph=True), h),
                              ("one_cta_graph", dict(graph=True), hp),
+                             ("prepass_model_graph", dict(graph=True), hs),
+                             ("in_kernel_graph", dict(graph=True), hf),
                              ("tuned_graph", dict(autotune=True, graph=True), h)]:
             t0 = time.perf_counter()
             plan = g.GroupedPlan(probs, mode=args.mode, h=hh, **kw)
@@ -734,6 +768,8 @@ def run_grouped(args):
                          "plan_create_s": create_s}
             plan.close()
         hp.close()
+        hf.close()
+        hs.close()
     best = res["tuned_graph"]
     print(json.dumps({"metric": "grouped GEMM TFLOP/s, 512 problems (2MNK summed)",
                       "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1,

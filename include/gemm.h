@@ -120,6 +120,29 @@ typedef enum {
     GEMM_LAYOUT_AS_STORED = 2
 } gemm_layout_t;
 
+/* split_place: where GEMM_MODE_BF16X3 splits FP32 operands into hi/lo BF16
+ * (the paper's packing step, Algorithm 1 / Section 3.1, with the split
+ * added).
+ *  GEMM_SPLIT_PREPASS (1): a bandwidth-bound pass writes the hi/lo planes to
+ *    workspace before the tensor-core kernel (8 bytes of HBM traffic per
+ *    element of A and B, two launches).
+ *  GEMM_SPLIT_IN_KERNEL (2): the tensor-core kernel reads the caller's FP32
+ *    A and B through TMA and splits each staged tile in shared memory
+ *    (converter warps), bit-identical to the pass; no split workspace.  It
+ *    runs one CTA per 128 x 256 tile with BK 32 (bn 0 or 256, bk 0 or 32,
+ *    cta_group 0 or 1, else GEMM_ERR_ARG) and needs A and B 16-byte aligned
+ *    with lda, ldb multiples of 4; other calls use the pass.  gemm() and
+ *    grouped plans only (gemm_from_host, gemm_syr2k use the pass).
+ *  GEMM_SPLIT_AUTO (0): the in-kernel split when the handle forces no tile
+ *    shape or layout and the pass would cost more than the kernel's lower
+ *    tensor-core rate (few-tile, skinny and small problems); grouped plans
+ *    take the faster of the two by the cost model or the autotuner. */
+typedef enum {
+    GEMM_SPLIT_AUTO = 0,
+    GEMM_SPLIT_PREPASS = 1,
+    GEMM_SPLIT_IN_KERNEL = 2
+} gemm_split_place_t;
+
 typedef struct {
     int32_t bn;
     int32_t bk;
@@ -131,7 +154,7 @@ typedef struct {
     int32_t cta_group;
     int64_t wait_poll_limit;
     int32_t operand_layout;
-    int32_t reserved; /* must be 0 */
+    int32_t split_place; /* gemm_split_place_t */
 } gemm_config_t;
 
 /* Create a handle bound to the CURRENT CUDA device.  Allocates a 256-byte

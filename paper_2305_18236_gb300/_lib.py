@@ -19,6 +19,8 @@ LOWER, UPPER = 0, 1
 UPLOS = {"lower": LOWER, "upper": UPPER}
 LAYOUT_AUTO, LAYOUT_K_MAJOR, LAYOUT_AS_STORED = 0, 1, 2
 LAYOUTS = {"auto": LAYOUT_AUTO, "k_major": LAYOUT_K_MAJOR, "as_stored": LAYOUT_AS_STORED}
+SPLIT_AUTO, SPLIT_PREPASS, SPLIT_IN_KERNEL = 0, 1, 2
+SPLIT_PLACES = {"auto": SPLIT_AUTO, "prepass": SPLIT_PREPASS, "in_kernel": SPLIT_IN_KERNEL}
 
 GEMM_OK = 0
 GEMM_ERR_ARG = -1
@@ -38,7 +40,7 @@ class gemm_config_t(ctypes.Structure):
     _fields_ = [("bn", _i32), ("bk", _i32), ("stages", _i32), ("split_k", _i32),
                 ("raster_group", _i32), ("max_ctas", _i32), ("promote_k", _i32),
                 ("cta_group", _i32), ("wait_poll_limit", _i64), ("operand_layout", _i32),
-                ("reserved", _i32)]
+                ("split_place", _i32)]
 
 
 class gemm_problem_t(ctypes.Structure):

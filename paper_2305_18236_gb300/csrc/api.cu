@@ -95,8 +95,21 @@ bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
 //    when packing pays (pack_pays); in their stored orientation otherwise,
 //    and always in grouped plans and SYR2K, whose transposing passes cost
 //    more than the kernel gains.
+// True when the in-kernel split is expected to beat the split pass plus the
+// faster pre-split kernel: the pass moves 8 bytes per element of A and B
+// (FP32 read, hi and lo written) and costs two launches; the kernel that
+// splits its own stages runs the tensor cores at about 3/5 of the rate of
+// the CTA-pair kernel on pre-split operands (rough GB300 rates).
+bool fuse_pays(int64_t M, int64_t N, int64_t K) {
+    const double m = double(M), n = double(N), k = double(K);
+    const double t_pass = 8.0 * (m * k + n * k) / 6.5e12 + 4e-6;
+    const double t_mma = 6.0 * m * n * k / 1.8e15;
+    return t_mma / 0.6 < t_pass + t_mma;
+}
+
 TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K, Call call,
-                 bool pack_a = false, bool pack_b = false, bool beta_zero = false) {
+                 bool pack_a = false, bool pack_b = false, bool beta_zero = false,
+                 bool f32_ok = false) {
     TcLaunch c;
     c.bn = h->cfg.bn ? h->cfg.bn : 256;
     if (call == Call::Syr2k) {
@@ -143,6 +156,19 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
         ((M + 255) / 256) * ((N + 511) / 512) >= h->num_sms / 2)
         c.bn = 512;
     if (c.bn == 512 && !wide_ok) c.bn = 256;
+    // In-kernel split (split precision on FP32 operands that TMA can read in
+    // place): one CTA per 128 x 256 tile with BK 32, operands as stored.
+    if (nterms == 3 && (call == Call::Split || call == Call::Grouped) && f32_ok &&
+        h->cfg.split_place != GEMM_SPLIT_PREPASS &&
+        (h->cfg.split_place == GEMM_SPLIT_IN_KERNEL ||
+         (h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.cta_group == 0 &&
+          h->cfg.operand_layout == GEMM_LAYOUT_AUTO && fuse_pays(M, N, K)))) {
+        c.fuse = 1;
+        c.cta_group = 1;
+        c.bn = 256;
+        c.bk = 32;
+        c.kmajor = 0;
+    }
     c.stages = h->cfg.stages;
     c.raster_group = h->cfg.raster_group ? h->cfg.raster_group : 16;
     c.max_ctas = h->cfg.max_ctas;
@@ -198,6 +224,20 @@ cudaError_t split_op(const OpPlan& o, int64_t rows, int64_t K, const float* X, i
 TcOperand operand_of(const OpPlan& o, const uint16_t* hi, int64_t rows, int64_t K, int planes) {
     TcOperand t{hi, rows, K, o.lay.ld, o.lay.plane, planes};
     t.mn_major = o.mn ? 1 : 0;
+    return t;
+}
+
+// An FP32 matrix TMA can read in place: 16-byte aligned base and row stride.
+bool f32_tma_ok(const float* X, int64_t ld) {
+    return (reinterpret_cast<uintptr_t>(X) & 15) == 0 && ld % 4 == 0;
+}
+
+// The caller's FP32 op(X) (rows x K) for the in-kernel split: stored K x rows
+// (MN-major tiles) or rows x K (K-major tiles).
+TcOperand f32_operand(const float* X, int64_t ld, int64_t rows, int64_t K, bool stored_k_rows) {
+    TcOperand t{nullptr, rows, K, ld, 0, 2};
+    t.mn_major = stored_k_rows ? 1 : 0;
+    t.f32 = X;
     return t;
 }
 
@@ -391,25 +431,35 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
         return run_simt(h, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
-    const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split, false, false, beta == 0.0f);
-    // op(A) is M x K and op(B)^T is N x K, split K-major or as stored
+    const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split, false, false, beta == 0.0f,
+                                 f32_tma_ok(A, lda) && f32_tma_ok(B, ldb));
+    // op(A) is M x K and op(B)^T is N x K, split K-major or as stored -- or,
+    // with the in-kernel split, read as stored in FP32 and split on chip
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
-    const WsPlan w = plan_ws(planes, pa.lay.plane, pb.lay.plane, M, N, K, cfg);
+    const WsPlan w = plan_ws(planes, cfg.fuse ? 0 : pa.lay.plane, cfg.fuse ? 0 : pb.lay.plane, M,
+                             N, K, cfg);
     uint8_t* ws;
     gemm_status_t st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
-    uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
-    uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
-    if (split_op(pa, M, K, A, lda, a_hi, planes, s) != cudaSuccess ||
-        split_op(pb, N, K, B, ldb, b_hi, planes, s) != cudaSuccess)
-        return GEMM_ERR_CUDA;
-    const TcOperand oa = operand_of(pa, a_hi, M, K, planes);
-    const TcOperand ob = operand_of(pb, b_hi, N, K, planes);
+    TcOperand oa, ob;
+    int launches = 0;
+    if (cfg.fuse) {
+        oa = f32_operand(A, lda, M, K, transA == GEMM_OP_T);
+        ob = f32_operand(B, ldb, N, K, transB == GEMM_OP_N);
+    } else {
+        uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
+        uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
+        if (split_op(pa, M, K, A, lda, a_hi, planes, s) != cudaSuccess ||
+            split_op(pb, N, K, B, ldb, b_hi, planes, s) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        oa = operand_of(pa, a_hi, M, K, planes);
+        ob = operand_of(pb, b_hi, N, K, planes);
+        launches = 2;
+    }
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
     float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
-    int launches = 2;
     int rc;
     {
         ProfScope prof(h, s);
@@ -447,6 +497,7 @@ bool handle_tile_auto(gemm_handle_t h) {
     // no tile shape, ring depth or CTA grouping forced by the handle
     return h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.stages == 0 && h->cfg.cta_group == 0;
 }
+int handle_split_place(gemm_handle_t h) { return h->cfg.split_place; }
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
     // tile choice of the handle's configuration (problem-size independent
     // parts) for grouped launches
@@ -542,7 +593,10 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         c.wait_poll_limit < 0 ||
         (c.operand_layout != GEMM_LAYOUT_AUTO && c.operand_layout != GEMM_LAYOUT_K_MAJOR &&
          c.operand_layout != GEMM_LAYOUT_AS_STORED) ||
-        c.reserved != 0)
+        (c.split_place != GEMM_SPLIT_AUTO && c.split_place != GEMM_SPLIT_PREPASS &&
+         c.split_place != GEMM_SPLIT_IN_KERNEL) ||
+        (c.split_place == GEMM_SPLIT_IN_KERNEL &&
+         ((c.bn != 0 && c.bn != 256) || (c.bk != 0 && c.bk != 32) || c.cta_group == 2)))
         return fail_arg(h, 2);
     h->cfg = c;
     return GEMM_OK;
@@ -721,7 +775,7 @@ gemm_status_t gemm_from_host(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB
     const bool tc = mode != GEMM_MODE_F32_SIMT;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
-    TcLaunch cfg = plan_tc(h, nterms, rb, N, K, Call::Split);
+    TcLaunch cfg = plan_tc(h, nterms, rb, N, K, Call::Split);  // split pass (no f32_ok)
     cfg.split_k = 1;
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);

@@ -124,7 +124,11 @@ int build_tables(const std::vector<HostProb>& ps, const TcLaunch& cfg,
 // the sustained tensor rate; smaller stages pay a per-stage issue cost that
 // no padding term shows (one CTA with BN 128 and BK 32 at 0.68), and one CTA
 // per tile stays below pairs per clock (0.90 with BN 256, BK 32).
-double config_efficiency(int cg, int bn, int bk) {
+// The in-kernel split (one CTA, BN 256, BK 32, `fused`) pays for its
+// converter warps with a lower rate than the same tiles on pre-split
+// operands, but needs no split pass.
+double config_efficiency(int cg, int bn, int bk, bool fused = false) {
+    if (fused) return 0.55;
     if (cg == 2) return bk == 64 ? 1.00 : 0.91;
     if (bn == 256) return bk == 32 ? 0.90 : 0.83;
     return bk == 64 ? 0.80 : 0.68;
@@ -132,16 +136,32 @@ double config_efficiency(int cg, int bn, int bk) {
 
 struct Candidate {
     TcLaunch cfg;
-    double model;
+    double model;  // seconds: kernel estimate, plus the split pass when it needs one
 };
 
+// Estimated seconds of the split pass over every operand: 8 bytes of HBM
+// traffic per element of A and B at about 5.8 TB/s.
+double split_pass_seconds(const std::vector<HostProb>& ps) {
+    double elems = 0.0;
+    for (const HostProb& q : ps) elems += double(q.M) * q.K + double(q.N) * q.K;
+    return 8.0 * elems / 5.8e12;
+}
+
+// Candidate configurations ranked by the model.  `prepass` / `fused` say
+// which split placements may be considered.
 std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nterms, int num_sms,
-                                       const TcLaunch& base) {
+                                       const TcLaunch& base, bool prepass = true,
+                                       bool fused = false) {
     std::vector<Candidate> out;
     const int kmax_smem = 232448;
+    const double t_split = split_pass_seconds(ps);
+    const double flop_per_mac = 2.0 * nterms;
+    for (int f : {0, 1}) {
+    if ((f == 0 && !prepass) || (f == 1 && (!fused || nterms != 3))) continue;
     for (int cg : {1, 2}) {
         for (int bn : {256, 128}) {
             for (int bk : {32, 64}) {
+                if (f == 1 && (cg != 1 || bn != 256 || bk != 32)) continue;  // fused shape
                 if (cg == 2 && (bn != 256 || nterms != 3)) continue;  // pair kernels compiled
                 int stages = 0;
                 for (int s = 8; s >= 2; --s)
@@ -167,10 +187,14 @@ std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nter
                 c.cfg.stages = stages;
                 c.cfg.split_k = 1;
                 c.cfg.cta_group = cg;
-                c.model = work * waves / config_efficiency(cg, bn, bk);
+                c.cfg.fuse = f;
+                c.cfg.kmajor = f ? 0 : base.kmajor;
+                c.model = flop_per_mac * work * waves / (1.8e15 * config_efficiency(cg, bn, bk, f)) +
+                          (f ? 0.0 : t_split);
                 out.push_back(c);
             }
         }
+    }
     }
     std::sort(out.begin(), out.end(),
               [](const Candidate& x, const Candidate& y) { return x.model < y.model; });
@@ -205,8 +229,8 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
         *out = it->second;
         return true;
     }
-    // optional persistent cache: lines "key bn bk stages raster cta_group"
-    // (lines without the last field are one-CTA configurations)
+    // optional persistent cache: lines "key bn bk stages raster cta_group fuse"
+    // (a missing cta_group means one CTA, a missing fuse the split pass)
     const char* path = getenv("GEMM_AUTOTUNE_CACHE");
     if (!path) return false;
     FILE* f = fopen(path, "r");
@@ -214,14 +238,15 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
     char line[256], k[128];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
-        int bn, bk, st, rg, cg = 1;
-        const int n = sscanf(line, "%127s %d %d %d %d %d", k, &bn, &bk, &st, &rg, &cg);
+        int bn, bk, st, rg, cg = 1, fu = 0;
+        const int n = sscanf(line, "%127s %d %d %d %d %d %d", k, &bn, &bk, &st, &rg, &cg, &fu);
         if (n < 5 || key != k) continue;
         out->bn = bn;
         out->bk = bk;
         out->stages = st;
         out->raster_group = rg;
         out->cta_group = cg == 2 ? 2 : 1;
+        out->fuse = fu == 1 ? 1 : 0;
         found = true;
     }
     fclose(f);
@@ -236,8 +261,8 @@ void cache_store(const std::string& key, const TcLaunch& c) {
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
-            c.cta_group);
+    fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
+            c.cta_group, c.fuse);
     fclose(f);
 }
 
@@ -333,6 +358,7 @@ void handle_set_err_arg(gemm_handle_t h, int pos);
 void handle_set_launches(gemm_handle_t h, int n);
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms);
 bool handle_tile_auto(gemm_handle_t h);
+int handle_split_place(gemm_handle_t h);
 }  // namespace gb300
 
 extern "C" {
@@ -382,13 +408,37 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     // grouped CTA-pair kernels exist for the split-precision mode with bn 256
     if (p->cfg.cta_group == 2 && (nterms != 3 || p->cfg.bn != 256)) p->cfg.cta_group = 1;
 
-    // Workspace layout: per problem, the hi (and lo) planes of A, then of B.
-    // An operand stored K x rows (A with transA, B without transB) keeps that
-    // orientation (MN-major tiles, split without transposing) unless the
-    // handle asks for K-major operands.
+    // Split placement.  The in-kernel split reads every A and B as stored
+    // through FP32 tensor maps, so each must be 16-byte aligned with a row
+    // stride that is a multiple of 4; it is considered when the handle asks
+    // for it, or under GEMM_SPLIT_AUTO when the handle forces no tile shape.
+    const int place = gb300::handle_split_place(h);
+    bool aligned = true;
+    for (int i = 0; i < count; ++i) {
+        const gemm_problem_t& q = hp[i];
+        if (q.M == 0 || q.N == 0 || q.K == 0 || q.alpha == 0.0f) continue;
+        aligned = aligned && (reinterpret_cast<uintptr_t>(q.A) & 15) == 0 && q.lda % 4 == 0 &&
+                  (reinterpret_cast<uintptr_t>(q.B) & 15) == 0 && q.ldb % 4 == 0;
+    }
+    const bool fused_ok = nterms == 3 && aligned && place != GEMM_SPLIT_PREPASS &&
+                          (place == GEMM_SPLIT_IN_KERNEL || gb300::handle_tile_auto(h));
+    const bool prepass_ok = !(fused_ok && place == GEMM_SPLIT_IN_KERNEL);
+    if (fused_ok && !prepass_ok) {  // the in-kernel split's one tile shape
+        p->cfg.fuse = 1;
+        p->cfg.cta_group = 1;
+        p->cfg.bn = 256;
+        p->cfg.bk = 32;
+        p->cfg.kmajor = 0;
+    }
+
+    // Workspace layout (split pass): per problem, the hi (and lo) planes of
+    // A, then of B.  An operand stored K x rows (A with transA, B without
+    // transB) keeps that orientation (MN-major tiles, split without
+    // transposing) unless the handle asks for K-major operands.
     auto a_mn = [&](const gemm_problem_t& q) { return q.transA != 0 && !p->cfg.kmajor; };
     auto b_mn = [&](const gemm_problem_t& q) { return q.transB == 0 && !p->cfg.kmajor; };
-    std::vector<HostProb> ps;
+    std::vector<HostProb> ps;    // operands as split-pass planes
+    std::vector<HostProb> ps_f;  // the same problems with FP32 operands (in-kernel split)
     std::vector<SplitJob> jobs;
     std::vector<int> tile_job, tile_job_t;
     int tiles_t = 0;
@@ -401,6 +451,24 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->scales.push_back({q.M, q.N, q.ldc, q.beta, q.C});
             continue;
         }
+        HostProb hq;
+        hq.M = q.M;
+        hq.N = q.N;
+        hq.K = q.K;
+        hq.ldc = q.ldc;
+        hq.alpha = q.alpha;
+        hq.beta = q.beta;
+        hq.C = q.C;
+        if (fused_ok) {
+            hq.a = TcOperand{nullptr, q.M, q.K, q.lda, 0, 2};
+            hq.a.mn_major = q.transA != 0;
+            hq.a.f32 = q.A;
+            hq.b = TcOperand{nullptr, q.N, q.K, q.ldb, 0, 2};
+            hq.b.mn_major = q.transB == 0;
+            hq.b.f32 = q.B;
+            ps_f.push_back(hq);
+        }
+        if (!prepass_ok) continue;
         a_off.push_back(ws);
         ws += round256(size_t(planes) * gb300::packed_layout(q.M, q.K, a_mn(q)).plane * 2);
         b_off.push_back(ws);
@@ -413,7 +481,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     }
     int tiles = 0;
     size_t idx = 0;
-    for (int i = 0; i < count; ++i) {
+    for (int i = 0; i < count && prepass_ok; ++i) {
         const gemm_problem_t& q = hp[i];
         if (q.M == 0 || q.N == 0 || q.K == 0 || q.alpha == 0.0f) continue;
         uint16_t* ah = reinterpret_cast<uint16_t*>(p->ws + a_off[idx]);
@@ -461,7 +529,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     p->njobs = int(jobs.size());
     p->split_tiles = tiles;
     p->split_tiles_t = tiles_t;
-    p->nprobs = int(ps.size());
+    p->nprobs = int(prepass_ok ? ps.size() : ps_f.size());
     gemm_status_t st = upload(&p->d_jobs, jobs, s);
     if (st == GEMM_OK) st = upload(&p->d_tile_job, tile_job, s);
     if (st == GEMM_OK) st = upload(&p->d_tile_job_t, tile_job_t, s);
@@ -469,14 +537,18 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         free_plan(p);
         return st;
     }
+    const std::vector<HostProb>& shapes = prepass_ok ? ps : ps_f;
 
-    if (!(flags & GEMM_GROUPED_AUTOTUNE) && !ps.empty() && gb300::handle_tile_auto(h)) {
-        // library choice without timing: the analytic model's best configuration
-        const std::vector<Candidate> cands = seed_candidates(ps, nterms, p->num_sms, p->cfg);
+    if (!(flags & GEMM_GROUPED_AUTOTUNE) && !shapes.empty() && gb300::handle_tile_auto(h)) {
+        // library choice without timing: the analytic model's best
+        // configuration and split placement
+        const std::vector<Candidate> cands =
+            seed_candidates(shapes, nterms, p->num_sms, p->cfg, prepass_ok, fused_ok);
         if (!cands.empty()) p->cfg = cands.front().cfg;
     }
-    if ((flags & GEMM_GROUPED_AUTOTUNE) && !ps.empty()) {
-        const std::string key = shape_key(p->num_sms, nterms, ps);
+    if ((flags & GEMM_GROUPED_AUTOTUNE) && !shapes.empty()) {
+        const std::string key = shape_key(p->num_sms, nterms, shapes) +
+                                (prepass_ok ? "-p" : "") + (fused_ok ? "-f" : "");
         TcLaunch hit = p->cfg;
         if (cache_lookup(key, &hit)) {
             p->cfg.bn = hit.bn;
@@ -484,14 +556,38 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->cfg.stages = hit.stages;
             p->cfg.raster_group = hit.raster_group;
             p->cfg.cta_group = hit.cta_group;
+            p->cfg.fuse = hit.fuse;
+            if (hit.fuse) p->cfg.kmajor = 0;
         } else {
-            // operands must be split before the candidates can be timed
-            if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs, p->split_tiles,
-                                            p->num_sms, s) != cudaSuccess ||
-                gb300::launch_split_grouped_t(p->d_jobs, p->d_tile_job_t, p->njobs,
-                                              p->split_tiles_t, p->num_sms, s) != cudaSuccess) {
-                free_plan(p);
-                return GEMM_ERR_CUDA;
+            // Operands must be split before the pre-split candidates can be
+            // timed; the pass's own time is added to theirs, so that both
+            // placements are compared over a whole plan run.
+            double split_ms = 0.0;
+            if (prepass_ok) {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                const bool ev = cudaEventCreate(&e0) == cudaSuccess &&
+                                cudaEventCreate(&e1) == cudaSuccess;
+                for (int rep = 0; rep < 2; ++rep) {  // the second run is timed
+                    if (ev) cudaEventRecord(e0, s);
+                    if (gb300::launch_split_grouped(p->d_jobs, p->d_tile_job, p->njobs,
+                                                    p->split_tiles, p->num_sms, s) != cudaSuccess ||
+                        gb300::launch_split_grouped_t(p->d_jobs, p->d_tile_job_t, p->njobs,
+                                                      p->split_tiles_t, p->num_sms,
+                                                      s) != cudaSuccess) {
+                        if (e0) cudaEventDestroy(e0);
+                        if (e1) cudaEventDestroy(e1);
+                        free_plan(p);
+                        return GEMM_ERR_CUDA;
+                    }
+                    if (ev) cudaEventRecord(e1, s);
+                }
+                float ms = 0.0f;
+                if (ev && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    split_ms = ms;
+                cudaGetLastError();
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
             }
             // Tune on the whole problem set when its outputs fit in scratch of at
             // most 4 GB and a quarter of the free device memory (the wave count
@@ -504,12 +600,14 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             }
             const size_t tune_cap =
                 std::max<size_t>(size_t(512) << 20, std::min<size_t>(size_t(4) << 30, free_b / 4));
-            std::vector<HostProb> sub;
+            std::vector<HostProb> sub, sub_f;
             size_t cbytes = 0;
-            for (const HostProb& q : ps) {
+            for (size_t i = 0; i < shapes.size(); ++i) {
+                const HostProb& q = shapes[i];
                 const size_t b = round256(size_t(q.M) * q.N * 4);
                 if (!sub.empty() && cbytes + b > tune_cap) break;
-                sub.push_back(q);
+                sub.push_back(prepass_ok ? ps[i] : ps_f[i]);
+                if (fused_ok) sub_f.push_back(ps_f[i]);
                 cbytes += b;
             }
             uint8_t* scratch = nullptr;
@@ -519,25 +617,42 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
                 return GEMM_ERR_WORKSPACE;
             }
             size_t off = 0;
-            for (HostProb& q : sub) {
-                q.C = reinterpret_cast<float*>(scratch + off);
-                q.ldc = q.N;
-                q.alpha = 1.0f;
-                q.beta = 0.0f;
-                off += round256(size_t(q.M) * q.N * 4);
+            for (size_t i = 0; i < sub.size(); ++i) {
+                for (std::vector<HostProb>* v : {&sub, &sub_f}) {
+                    if (i >= v->size()) continue;
+                    HostProb& q = (*v)[i];
+                    q.C = reinterpret_cast<float*>(scratch + off);
+                    q.ldc = q.N;
+                    q.alpha = 1.0f;
+                    q.beta = 0.0f;
+                }
+                off += round256(size_t(sub[i].M) * sub[i].N * 4);
             }
-            std::vector<Candidate> cands = seed_candidates(sub, nterms, p->num_sms, p->cfg);
+            // the split pass covers the whole set; scale its time to the subset
+            const double frac = split_pass_seconds(sub) / std::max(1e-30, split_pass_seconds(shapes));
+            std::vector<Candidate> cands =
+                seed_candidates(sub, nterms, p->num_sms, p->cfg, prepass_ok, fused_ok);
             double best = -1.0;
             TcLaunch best_cfg = p->cfg;
-            const size_t tries = std::min<size_t>(cands.size(), 4);
-            for (size_t c = 0; c < tries; ++c) {
+            // the model's four best, plus the best of the placement it ranks lower
+            std::vector<Candidate> tries(cands.begin(),
+                                         cands.begin() + std::min<size_t>(cands.size(), 4));
+            for (const Candidate& c : cands)
+                if (c.cfg.fuse != tries.front().cfg.fuse) {
+                    bool have = false;
+                    for (const Candidate& t : tries) have = have || t.cfg.fuse == c.cfg.fuse;
+                    if (!have) tries.push_back(c);
+                    break;
+                }
+            for (const Candidate& cand : tries) {
                 for (int rg : {8, 16}) {
-                    TcLaunch cfg = cands[c].cfg;
+                    TcLaunch cfg = cand.cfg;
                     cfg.raster_group = rg;
-                    const double ms =
-                        time_candidate(sub, nterms, cfg, p->err_word, p->num_sms, s);
-                    if (ms > 0.0 && (best < 0.0 || ms < best)) {
-                        best = ms;
+                    const double ms = time_candidate(cfg.fuse ? sub_f : sub, nterms, cfg,
+                                                     p->err_word, p->num_sms, s);
+                    const double total = ms + (cfg.fuse ? 0.0 : split_ms * frac);
+                    if (ms > 0.0 && (best < 0.0 || total < best)) {
+                        best = total;
                         best_cfg = cfg;
                     }
                 }
@@ -550,12 +665,19 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             }
         }
     }
+    if (p->cfg.fuse) {
+        // no split pass: drop its workspace and tables
+        if (p->ws) cudaFree(p->ws);
+        p->ws = nullptr;
+        p->njobs = p->split_tiles = p->split_tiles_t = 0;
+        p->nprobs = int(ps_f.size());
+    }
 
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
     bool ok = true;
-    p->total_tiles = build_tables(ps, p->cfg, probs, maps, tile_prob, &ok);
+    p->total_tiles = build_tables(p->cfg.fuse ? ps_f : ps, p->cfg, probs, maps, tile_prob, &ok);
     if (!ok) {
         free_plan(p);
         return GEMM_ERR_CUDA;
@@ -614,7 +736,7 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg
         cfg->cta_group = p->cfg.cta_group;
         cfg->wait_poll_limit = p->cfg.poll_limit;
         cfg->operand_layout = p->cfg.kmajor ? GEMM_LAYOUT_K_MAJOR : GEMM_LAYOUT_AS_STORED;
-        cfg->reserved = 0;
+        cfg->split_place = p->cfg.fuse ? GEMM_SPLIT_IN_KERNEL : GEMM_SPLIT_PREPASS;
     }
     if (tuned_ms) *tuned_ms = p->tuned_ms;
     return GEMM_OK;

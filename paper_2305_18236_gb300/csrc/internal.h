@@ -20,6 +20,7 @@ struct TcLaunch {
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
     int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)
     int kmajor = 0;          // 1: every operand K-major (transposing split / pack)
+    int fuse = 0;            // 1: split FP32 operands inside the kernel (TcOperand::f32)
 };
 
 // One operand of the tensor-core kernel: BF16, `planes` stacked planes
@@ -37,6 +38,10 @@ struct TcOperand {
     int planes;
     int mn_major = 0;
     int box_planes = 0;  // planes one TMA box copies (0 = all); SYR2K buffers hold two matrices
+    // In-kernel split: the caller's FP32 matrix (base unused), `ld` in FP32
+    // elements, 16-byte aligned with ld % 4 == 0 (TMA); the kernel splits it
+    // into hi/lo planes in shared memory.
+    const float* f32 = nullptr;
 };
 
 // Row stride and plane size (elements) of an operand written by the split

@@ -17,21 +17,17 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "split_bf16.cuh"
 
 namespace gb300 {
 
 namespace {
 
 __device__ __forceinline__ void split1(float x, uint16_t& h, uint16_t& l) {
-    const __nv_bfloat16 hb = __float2bfloat16_rn(x);
-    const float hv = __bfloat162float(hb);
-    h = __bfloat16_as_ushort(hb);
-    l = isfinite(hv) ? __bfloat16_as_ushort(__float2bfloat16_rn(x - hv)) : uint16_t(0);
+    split_bf16_1(x, h, l);
 }
 
-__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
-    return uint32_t(a) | (uint32_t(b) << 16);
-}
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return pack_bf16x2(a, b); }
 
 int grid_for(int64_t work, int per_block) {
     static int sms_of[64] = {};  // SM count per device, queried once

@@ -25,7 +25,9 @@
 // Warp roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM owner and
 // MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31
 // and one half of the tile's columns); the plain-BF16 CTA-pair kernel adds
-// warp 10, which issues the B copies (352 threads).
+// warp 10, which issues the B copies (352 threads).  With the in-kernel
+// split (FUSE, 512 threads) the epilogue is warps 4-11 and warps 2-3 and
+// 12-15 split FP32 stages into hi/lo in shared memory.
 // Two accumulators (2 x BN TMEM columns) let the epilogue of tile i overlap
 // the MMAs of tile i+1.  Every wait is bounded (ptx.cuh); on expiry the
 // kernel records the error, drains its own copies and MMAs, frees TMEM and
@@ -41,6 +43,7 @@
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "split_bf16.cuh"
 
 namespace gb300 {
 
@@ -49,6 +52,17 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kEpiWarps = 8;               // warps 2..9
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue
+// In-kernel split (FUSE): 16 warps in four warpgroups -- warp 0 producer,
+// warp 1 MMA, warps 2-3 and 12-15 split FP32 stages into hi/lo in place,
+// warps 4-11 epilogue.  Registers are handed to a CTA per warpgroup; the
+// epilogue warpgroups take 200 a thread (128 running FP32 sums), the others
+// 56 (setmaxnreg): 256 x 200 + 256 x 56 = 65536 = 512 x 128.
+constexpr int kFusedThreads = 512;
+constexpr int kConvWarps = 6;
+constexpr int kFusedEpi0 = 4;  // first epilogue warp
+constexpr int kFusedEpiRegs = 200;
+constexpr int kFusedOtherRegs = 56;
+static_assert(256 * kFusedEpiRegs + 256 * kFusedOtherRegs <= 65536, "register split");
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in dynamic shared memory per block
 
 struct TcParams {
@@ -353,6 +367,67 @@ __device__ __forceinline__ OpLayout op_layout(int mn, int plane_bytes) {
     return l;
 }
 
+// Layout of an operand whose FP32 tile was split in place (FUSE): each
+// group of 8 rows (K-major: operand rows; MN-major: K indices) that TMA
+// wrote as 8 x W FP32 values becomes [hi atom][lo atom] of 8 rows of 2W
+// bytes, so consecutive 8-row groups of the hi plane are 32 W bytes apart
+// and the lo plane is 16 W bytes further on.  K-major: W = BK (64-byte
+// swizzle for BK 32, 128-byte for BK 64).  MN-major: W = 64 MN elements
+// (128-byte swizzle), 64-element groups MN_GROUP apart, a 16-deep K slice
+// two 8-row groups down.
+template <class S>
+__device__ __forceinline__ OpLayout op_layout_fused(int mn) {
+    OpLayout l;
+    if (mn) {
+        l.fields = sdesc_fields(S::MN_GROUP, 2048, 2);
+        l.lo_off = 1024;
+        l.k_step = 4096;
+    } else {
+        l.fields = sdesc_fields(16, 16 * S::ROW_BYTES, S::ROW_BYTES == 128 ? 2 : 4);
+        l.lo_off = 8 * S::ROW_BYTES;
+        l.k_step = 32;
+    }
+    return l;
+}
+
+// The in-kernel split of one group (the packing step moved on chip): at
+// shared address g, TMA left 8 rows of W FP32 values (row r at 4 W r bytes,
+// no swizzle); they become, in place, the hi atom at g and the lo atom at
+// g + 16 W: 8 rows of 2 W bytes in the swizzled layout the MMA reads, the
+// 16-byte chunk c of row r stored at chunk c ^ (r mod 8) (128-byte swizzle,
+// W = 64) or c ^ ((r / 2) mod 4) (64-byte swizzle, W = 32).  Lane l's i-th
+// 16-byte load covers row (512 i + 16 l) / 4W, 4 consecutive columns; its
+// two 8-byte stores go to group_store_offset<W>(i, l) and 16 W further on.
+// The warp reads the whole group before any lane writes.  The split is
+// split_bf16_2, bit-identical to the split pass.
+template <int W>
+__device__ __forceinline__ uint32_t group_store_offset(int i, int lane) {
+    const int o = i * 512 + lane * 16;
+    const int r = o / (W * 4);
+    const int c0 = (o % (W * 4)) / 4;  // first of the lane's 4 columns
+    const int sw = W == 64 ? (r & 7) : ((r >> 1) & 3);
+    return uint32_t(r * (W * 2) + (((c0 >> 3) ^ sw) << 4) + (c0 & 7) * 2);
+}
+
+template <int W>
+__device__ __forceinline__ void split_group_in_place(uint32_t g, int lane,
+                                                     const uint32_t (&off)[8 * W * 4 / 512]) {
+    static_assert(W == 32 || W == 64, "row width");
+    constexpr int N4 = 8 * W * 4 / 512;  // 16-byte loads per lane
+    float4 v[N4];
+#pragma unroll
+    for (int i = 0; i < N4; ++i) v[i] = ld_shared_f4(g + i * 512 + lane * 16);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < N4; ++i) {
+        uint32_t h01, h23, l01, l23;
+        split_bf16_2(v[i].x, v[i].y, h01, l01);
+        split_bf16_2(v[i].z, v[i].w, h23, l23);
+        st_shared_v2(g + off[i], h01, h23);
+        st_shared_v2(g + 16 * W + off[i], l01, l23);
+    }
+}
+
 // The same in descriptor units: the descriptor of the operand's hi tile in
 // ring slot 0, and what a lo plane and a 16-deep K slice add to it.  The
 // start-address field holds address / 16 in 14 bits and shared memory ends
@@ -388,11 +463,18 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
     }
 }
 
-template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
-__global__ void __launch_bounds__(kThreads, 1)
+// FUSE (split precision only): the operands are the caller's FP32 matrices;
+// TMA stages FP32 tiles, converter warps split them in place into the hi/lo
+// atoms the MMA reads (split_group_in_place) and arrive on conv[s], which
+// the MMA issuer waits on instead of full[s]; no split pass runs before the
+// kernel.
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED, bool FUSE = false>
+__global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcParams p) {
     using S = Shape<BN, BK, NTERMS>;
+    static_assert(!FUSE || NTERMS == 3, "the in-kernel split feeds the split-precision MMAs");
+    constexpr int EPI0 = FUSE ? kFusedEpi0 : 2;  // first epilogue warp
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~uintptr_t(1023));
@@ -403,7 +485,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* acc_full = empty + stages;  // [2]
     uint64_t* acc_empty = acc_full + 2;   // [2]
     uint64_t* drain = acc_empty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* conv = drain + 1;  // FUSE: [stages], stage s split in place
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(FUSE ? conv + stages : drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* staging = reinterpret_cast<float*>(bar_area + S::BAR_BYTES);  // [kEpiWarps][32][33]
 
@@ -414,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+            if (FUSE) mbar_init(&conv[s], kConvWarps);  // one arrival per converter warp
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
@@ -436,125 +520,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            const uint64_t pol = l2_policy_evict_last();
-            uint32_t filled = 0;      // bit s: slot s received a fill
-            uint32_t fill_par = 0;    // bit s: parity of slot s's latest fill
-            int s = 0;                // ring slot of the next fill
-            uint32_t ph = 0;          // and its parity
-            bool ok = true;
-            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
-                for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
-                    if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
-                        ok = false;
-                        break;
-                    }
-                    // SYR2K: K blocks [0, syr_kb) pair A-side rows of the first
-                    // matrix with B-side rows of the second, the next syr_kb
-                    // blocks the other way round (the two GEMM updates of a block)
-                    int kc = kb, za = 0, zb = 0;
-                    if (!GROUPED && p.syr_kb > 0) {
-                        const int second = kb >= p.syr_kb;
-                        kc = kb - (second ? p.syr_kb : 0);
-                        za = second ? p.syr_plane : 0;
-                        zb = second ? 0 : p.syr_plane;
-                    }
-                    uint8_t* st = smem + s * S::STAGE;
-                    mbar_arrive_expect_tx(&full[s], S::STAGE);
-                    load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kc * BK,
-                                 ti.mt * kBM, za, pol);
-                    load_operand(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], (ti.maj >> 1) & 1,
-                                 BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol);
-                    filled |= 1u << s;
-                    fill_par = (fill_par & ~(1u << s)) | (ph << s);
-                    if (++s == stages) {
-                        s = 0;
-                        ph ^= 1;
-                    }
-                }
-            }
-            // Wait for every copy this thread started before the CTA may exit.
-            for (int s = 0; s < stages; ++s)
-                if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            // One thread issues every MMA, so its per-stage instruction path
-            // is on the critical path of the tensor pipe: ring slot and parity
-            // are running counters and descriptors are built with adds.
-            int g = 0;        // accumulation chunks started by this CTA
-            int s = 0;        // ring slot of the next stage to consume
-            uint32_t ph = 0;  // and its fill parity
-            bool ok = true;
-            const uint32_t slot0 = smem_u32(smem);
-            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
-                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
-                const int kb0 = ti.kb0, kb1 = ti.kb1;
-                const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
-                const uint32_t idesc = make_idesc_bf16_f32(kBM, BN, a_mn, b_mn);
-                const OpDesc da = op_desc(slot0, op_layout<S>(a_mn, S::A_PLANE));
-                const OpDesc db =
-                    op_desc(slot0 + S::PLANES * S::A_PLANE, op_layout<S>(b_mn, S::B_PLANE));
-                const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
-                for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
-                    const int buf = g & 1;
-                    const uint32_t acc_ph = (g >> 1) & 1;
-                    if (!mbar_wait_bounded(&acc_empty[buf], acc_ph ^ 1, p.lim, abort_flag, p.err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + buf * BN;
-                    const int c1 = min(c0 + chunk, kb1);
-                    for (int kb = c0; kb < c1; ++kb) {
-                        if (!mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t slot16 = uint32_t(s) * uint32_t(S::STAGE >> 4);
-                        const uint64_t a_s = da.d0 + slot16, b_s = db.d0 + slot16;
-#pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint64_t ah = a_s + uint32_t(kk) * da.k16;
-                            const uint64_t bh = b_s + uint32_t(kk) * db.k16;
-                            const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
-                            if (NTERMS == 3) {
-                                umma_bf16(d_tmem, ah + da.lo16, bh, idesc, acc);
-                                umma_bf16(d_tmem, ah, bh + db.lo16, idesc, 1u);
-                                umma_bf16(d_tmem, ah, bh, idesc, 1u);
-                            } else {
-                                umma_bf16(d_tmem, ah, bh, idesc, acc);
-                            }
-                        }
-                        umma_commit(&empty[s]);  // slot free once these MMAs have read it
-                        if (++s == stages) {
-                            s = 0;
-                            ph ^= 1;
-                        }
-                    }
-                    if (!ok) break;
-                    umma_commit(&acc_full[buf]);  // chunk ready for the epilogue
-                }
-            }
-            // All MMAs this thread issued must finish before TMEM is freed.
-            umma_commit(drain);
-            mbar_wait_drain(drain, 0, p.err);
-        }
-    } else {
+    // Role dispatch, epilogue first: with FUSE the epilogue warpgroups raise
+    // their register budget and the others (producer, MMA issuer, converters)
+    // lower theirs at the head of their branch, so that the raised budget
+    // covers the epilogue code (warpgroups 0 and 3 execute the same lowering).
+    if (FUSE ? (warp >= EPI0 && warp < EPI0 + kEpiWarps) : warp >= 2) {
+        if constexpr (FUSE) regs_inc<kFusedEpiRegs>();
         // ------------------------------------------------ epilogue
         // Warp w reads TMEM lanes 32*(w%4)..+31 (tile rows) and one half of
         // the tile's columns.
         constexpr int COLS = BN / 2;     // columns per epilogue warp
         constexpr int PIECES = COLS / 32;
         const int ew = warp & 3;
-        const int col_base = ((warp - 2) >> 2) * COLS;
-        float* stg = staging + (warp - 2) * 32 * 33;
-        float* slab = staging + (warp - 2) * 1024;  // 4 KB, 1024-byte aligned (TMA store)
+        const int col_base = ((warp - EPI0) >> 2) * COLS;
+        float* stg = staging + (warp - EPI0) * 32 * 33;
+        float* slab = staging + (warp - EPI0) * 1024;  // 4 KB, 1024-byte aligned (TMA store)
         float sum[PROMOTE ? COLS : 1];
         int g = 0;
         bool ok = true;
@@ -639,6 +619,175 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                }
+            }
+        }
+    } else {
+        if constexpr (FUSE) regs_dec<kFusedOtherRegs>();
+        if (warp == 0) {
+            // ------------------------------------------------ TMA producer
+            if (lane == 0) {
+                const uint64_t pol = l2_policy_evict_last();
+                uint32_t filled = 0;      // bit s: slot s received a fill
+                uint32_t fill_par = 0;    // bit s: parity of slot s's latest fill
+                int s = 0;                // ring slot of the next fill
+                uint32_t ph = 0;          // and its parity
+                bool ok = true;
+                for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                    const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+                    for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
+                        if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        // SYR2K: K blocks [0, syr_kb) pair A-side rows of the first
+                        // matrix with B-side rows of the second, the next syr_kb
+                        // blocks the other way round (the two GEMM updates of a block)
+                        int kc = kb, za = 0, zb = 0;
+                        if (!GROUPED && p.syr_kb > 0) {
+                            const int second = kb >= p.syr_kb;
+                            kc = kb - (second ? p.syr_kb : 0);
+                            za = second ? p.syr_plane : 0;
+                            zb = second ? 0 : p.syr_plane;
+                        }
+                        uint8_t* st = smem + s * S::STAGE;
+                        mbar_arrive_expect_tx(&full[s], S::STAGE);
+                        load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kc * BK,
+                                     ti.mt * kBM, za, pol);
+                        load_operand(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], (ti.maj >> 1) & 1,
+                                     BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol);
+                        filled |= 1u << s;
+                        fill_par = (fill_par & ~(1u << s)) | (ph << s);
+                        if (++s == stages) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                    }
+                }
+                // Wait for every copy this thread started before the CTA may exit.
+                for (int s = 0; s < stages; ++s)
+                    if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
+            }
+        } else if (warp == 1) {
+            // ------------------------------------------------ MMA issuer
+            if (lane == 0) {
+                // One thread issues every MMA, so its per-stage instruction path
+                // is on the critical path of the tensor pipe: ring slot and parity
+                // are running counters and descriptors are built with adds.
+                int g = 0;        // accumulation chunks started by this CTA
+                int s = 0;        // ring slot of the next stage to consume
+                uint32_t ph = 0;  // and its fill parity
+                bool ok = true;
+                const uint32_t slot0 = smem_u32(smem);
+                for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                    const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+                    const int kb0 = ti.kb0, kb1 = ti.kb1;
+                    const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
+                    const uint32_t idesc = make_idesc_bf16_f32(kBM, BN, a_mn, b_mn);
+                    const OpDesc da = op_desc(slot0, FUSE ? op_layout_fused<S>(a_mn)
+                                                          : op_layout<S>(a_mn, S::A_PLANE));
+                    const OpDesc db = op_desc(slot0 + S::PLANES * S::A_PLANE,
+                                              FUSE ? op_layout_fused<S>(b_mn)
+                                                   : op_layout<S>(b_mn, S::B_PLANE));
+                    const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
+                    for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
+                        const int buf = g & 1;
+                        const uint32_t acc_ph = (g >> 1) & 1;
+                        if (!mbar_wait_bounded(&acc_empty[buf], acc_ph ^ 1, p.lim, abort_flag, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + buf * BN;
+                        const int c1 = min(c0 + chunk, kb1);
+                        for (int kb = c0; kb < c1; ++kb) {
+                            // FUSE: the stage is usable once it has been split in place
+                            if (!mbar_wait_bounded(FUSE ? &conv[s] : &full[s], ph, p.lim, abort_flag,
+                                                   p.err)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t slot16 = uint32_t(s) * uint32_t(S::STAGE >> 4);
+                            const uint64_t a_s = da.d0 + slot16, b_s = db.d0 + slot16;
+    #pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                const uint64_t ah = a_s + uint32_t(kk) * da.k16;
+                                const uint64_t bh = b_s + uint32_t(kk) * db.k16;
+                                const uint32_t acc = (kb > c0 || kk > 0) ? 1u : 0u;
+                                if (NTERMS == 3) {
+                                    umma_bf16(d_tmem, ah + da.lo16, bh, idesc, acc);
+                                    umma_bf16(d_tmem, ah, bh + db.lo16, idesc, 1u);
+                                    umma_bf16(d_tmem, ah, bh, idesc, 1u);
+                                } else {
+                                    umma_bf16(d_tmem, ah, bh, idesc, acc);
+                                }
+                            }
+                            umma_commit(&empty[s]);  // slot free once these MMAs have read it
+                            if (++s == stages) {
+                                s = 0;
+                                ph ^= 1;
+                            }
+                        }
+                        if (!ok) break;
+                        umma_commit(&acc_full[buf]);  // chunk ready for the epilogue
+                    }
+                }
+                // All MMAs this thread issued must finish before TMEM is freed.
+                umma_commit(drain);
+                mbar_wait_drain(drain, 0, p.err);
+            }
+        } else if constexpr (FUSE) {
+            // ------------------------------------------------ converters (FUSE)
+            // Converter cw of 6 splits every 6th 8-row group of each stage: the A
+            // groups first, then the B groups.  All lanes wait for the stage (the
+            // copies' writes become visible to each waiting thread), split, make
+            // their shared-memory writes visible to the tensor core (proxy
+            // fence), and lane 0 arrives on conv[s] once the warp has finished.
+            const int cw = warp < EPI0 ? warp - 2 : warp - (EPI0 + kEpiWarps) + 2;
+            const uint32_t slot0 = smem_u32(smem);
+            uint32_t off32[2], off64[4];  // this lane's store offsets in a group
+#pragma unroll
+            for (int i = 0; i < 2; ++i) off32[i] = group_store_offset<32>(i, lane);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) off64[i] = group_store_offset<64>(i, lane);
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+    #pragma unroll 1
+            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
+                const int wa = (ti.maj & 1) ? 64 : BK;         // row width of an A group
+                const int wb = ((ti.maj >> 1) & 1) ? 64 : BK;  // and of a B group
+                const int na = kBM * BK * 4 / (32 * wa);       // groups of 32 W bytes
+                const int nb = BN * BK * 4 / (32 * wb);
+    #pragma unroll 1
+                for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
+                    const bool got = mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err);
+                    if (!__all_sync(0xffffffffu, got)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = slot0 + uint32_t(s) * uint32_t(S::STAGE);
+    #pragma unroll 1
+                    for (int gi = cw; gi < na + nb; gi += kConvWarps) {
+                        const bool in_a = gi < na;
+                        const int w = in_a ? wa : wb;
+                        const uint32_t g = in_a ? st + uint32_t(gi * 32 * wa)
+                                                : st + uint32_t(S::PLANES * S::A_PLANE) +
+                                                      uint32_t((gi - na) * 32 * wb);
+                        if (w == 64)
+                            split_group_in_place<64>(g, lane, off64);
+                        else
+                            split_group_in_place<32>(g, lane, off32);
+                    }
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&conv[s]);
+                    if (++s == stages) {
+                        s = 0;
+                        ph ^= 1;
+                    }
                 }
             }
         }
@@ -1128,7 +1277,7 @@ bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
     return true;
 }
 
-template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED>
+template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED, bool FUSE = false>
 int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
                    TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
     using S = Shape<BN, BK, NTERMS>;
@@ -1139,14 +1288,14 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
     const int smem = std::max(S::smem_bytes(stages), min_smem);
-    auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE, GROUPED>;
+    auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE, GROUPED, FUSE>;
     static std::atomic<uint64_t> smem_set{0};  // bit d: limit raised on device d
     if (!allow_max_smem(kern, smem_set)) return -4;
     int ctas = num_sms;
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
     if (ctas < 1) ctas = 1;
-    kern<<<ctas, kThreads, smem, stream>>>(ta, tb, tc, p);
+    kern<<<ctas, FUSE ? kFusedThreads : kThreads, smem, stream>>>(ta, tb, tc, p);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
@@ -1196,6 +1345,7 @@ int dispatch_pair(int nterms, bool promote, int bn, int bk, const CUtensorMap& t
     GB300_PAIR_CASE(256, 32, 3, true)
     GB300_PAIR_CASE(256, 64, 3, true)
     GB300_PAIR_CASE(256, 32, 3, false)
+    GB300_PAIR_CASE(256, 64, 3, false)
     GB300_PAIR_CASE(256, 64, 1, false)
     GB300_PAIR_CASE(256, 32, 1, false)
     GB300_PAIR_CASE(512, 64, 1, false)
@@ -1207,6 +1357,13 @@ template <bool GROUPED>
 int dispatch(int nterms, bool promote, int bn, int bk, const CUtensorMap& ta,
              const CUtensorMap& tb, const CUtensorMap& tc, const TcParams& p, const TcLaunch& cfg,
              int num_sms, cudaStream_t s) {
+    if (cfg.fuse) {  // in-kernel split: split precision, 128 x 256 tiles, BK 32
+        if (nterms != 3 || bn != 256 || bk != 32) return -6;
+        return promote ? launch_variant<256, 32, 3, true, GROUPED, true>(ta, tb, tc, p, cfg,
+                                                                          num_sms, s)
+                       : launch_variant<256, 32, 3, false, GROUPED, true>(ta, tb, tc, p, cfg,
+                                                                           num_sms, s);
+    }
 #define GB300_TC_CASE(BN_, BK_, NT_, PR_)                                                      \
     if (bn == BN_ && bk == BK_ && nterms == NT_ && promote == PR_)                             \
         return launch_variant<BN_, BK_, NT_, PR_, GROUPED>(ta, tb, tc, p, cfg, num_sms, s);
@@ -1255,6 +1412,21 @@ bool encode_operand(CUtensorMap* map, const TcOperand& op, int bk, int box_rows)
     auto fn = encode_fn();
     if (!fn) return false;
     if (op.mn_major && box_rows % 64 != 0) return false;
+    if (op.f32) {
+        // FP32 operand for the in-kernel split: unswizzled boxes (bk, box_rows)
+        // K-major or (64, bk) MN-major, a third extent of 1 so that the
+        // kernel's 3-D copies address it like a one-plane buffer
+        const int64_t stored_rows = op.mn_major ? op.k : op.rows;
+        cuuint64_t dims[3] = {cuuint64_t(op.mn_major ? op.rows : op.k), cuuint64_t(stored_rows), 1};
+        cuuint64_t strides[2] = {cuuint64_t(op.ld) * 4, cuuint64_t(op.ld) * stored_rows * 4};
+        cuuint32_t box[3] = {cuuint32_t(op.mn_major ? 64 : bk),
+                             cuuint32_t(op.mn_major ? bk : box_rows), 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(op.f32), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     // stored rows: operand rows (K-major) or K indices (MN-major)
     const int64_t stored_rows = op.mn_major ? op.k : op.rows;
     cuuint64_t dims[3] = {cuuint64_t(op.mn_major ? op.rows : op.k), cuuint64_t(stored_rows),
@@ -1323,7 +1495,10 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     } else if (beta == 0.0f && (reinterpret_cast<uintptr_t>(C) & 15) == 0 && ldc % 4 == 0) {
         p.c_tma = encode_output(&tc, C, M, N, ldc, 1);
     }
-    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    // A tile whose K range is one accumulation chunk has nothing to promote:
+    // the kernel without promotion stores the same TMEM sums, bit for bit,
+    // without holding them in registers first.
+    const bool promote = nterms == 3 && cfg.promote_k > 0 && p.kb_per_split > p.chunk_kb;
     const int rc = pair ? dispatch_pair<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
                                                stream)
                         : dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
@@ -1377,7 +1552,7 @@ int launch_tc_syr2k(const TcOperand& xy, int nterms, int uplo, int64_t N, int64_
     CUtensorMap ta, tb, tc{};
     if (!encode_operand(&ta, xy, bk, kBM) || !encode_operand(&tb, xy, bk, bn)) return -4;
     p.c_tma = 0;  // diagonal tiles store only their triangle
-    const bool promote = nterms == 3 && cfg.promote_k > 0;
+    const bool promote = nterms == 3 && cfg.promote_k > 0 && p.k_blocks > p.chunk_kb;
     const int rc = dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream);
     if (rc != 0) return rc;
     if (launches) *launches += 1;

@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import LAYOUTS, MODES, check, gemm_config_t, gemm_problem_t
+from ._lib import LAYOUTS, MODES, SPLIT_PLACES, check, gemm_config_t, gemm_problem_t
 
 __all__ = ["Gemm", "handle", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
            "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "sync"]
@@ -69,13 +69,17 @@ class Gemm:
 
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
-                   promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="auto"):
+                   promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="auto",
+                   split_place="auto"):
         """operand_layout: "auto" (library choice), "as_stored" (MN-major tiles
         for operands stored K x rows) or "k_major" (every operand made
-        K-contiguous first)."""
+        K-contiguous first).  split_place (3xBF16): "auto", "prepass" (split
+        pass before the kernel) or "in_kernel" (the kernel splits FP32 tiles
+        in shared memory)."""
         layout = LAYOUTS[operand_layout] if isinstance(operand_layout, str) else operand_layout
+        place = SPLIT_PLACES[split_place] if isinstance(split_place, str) else split_place
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
-                            wait_poll_limit, layout, 0)
+                            wait_poll_limit, layout, place)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
         self._ws_sizes.clear()
 
@@ -305,9 +309,11 @@ class GroupedPlan:
         check(self.lib.gemm_grouped_plan_config(self.plan, ctypes.byref(cfg), ctypes.byref(ms)),
               "gemm_grouped_plan_config")
         names = {v: k for k, v in LAYOUTS.items()}
+        places = {v: k for k, v in SPLIT_PLACES.items()}
         return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
                 "raster_group": cfg.raster_group, "cta_group": cfg.cta_group,
                 "operand_layout": names.get(cfg.operand_layout, cfg.operand_layout),
+                "split_place": places.get(cfg.split_place, cfg.split_place),
                 "tuned_ms": ms.value}
 
     def close(self):
