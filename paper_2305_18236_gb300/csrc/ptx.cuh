@@ -82,6 +82,28 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// The same for a wait that is expected to last (an epilogue waiting for a
+// whole accumulation chunk): after the first few polls the thread sleeps
+// `sleep_ns` between polls, so that its issue slots go to the warps that do
+// the work meanwhile.
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t* bar, uint32_t parity,
+                                                        WaitLimit lim, volatile int* abort,
+                                                        int* err_word, unsigned sleep_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (long long i = 1; i < lim.polls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 4) __nanosleep(sleep_ns);
+        if ((i & 63) == 0 || i >= 4) {
+            if (*abort) return false;
+            if (global_timer_ns() - t0 > lim.ns) break;
+        }
+    }
+    *abort = 1;
+    atomicOr(err_word, kErrWaitTimeout);
+    return false;
+}
+
 // Teardown wait for work this thread itself started (TMA copies, MMAs):
 // not cut short by the abort flag, bounded on its own.
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, int* err_word) {

@@ -551,7 +551,10 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 const uint32_t acc_ph = (g >> 1) & 1;
                 int got = 0;
                 if (lane == 0)
-                    got = mbar_wait_bounded(&acc_full[buf], acc_ph, p.lim, abort_flag, p.err);
+                    got = FUSE ? mbar_wait_bounded_sleep(&acc_full[buf], acc_ph, p.lim, abort_flag,
+                                                         p.err, 256)
+                               : mbar_wait_bounded(&acc_full[buf], acc_ph, p.lim, abort_flag,
+                                                   p.err);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) {
                     ok = false;
@@ -763,7 +766,13 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 const int nb = BN * BK * 4 / (32 * wb);
     #pragma unroll 1
                 for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
-                    const bool got = mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err);
+                    // lane 0 polls; then every lane observes the completed
+                    // phase itself (one try_wait that succeeds at once), so
+                    // the copies' writes are visible to the whole warp
+                    int got = 0;
+                    if (lane == 0) got = mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err);
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (got) got = mbar_wait_bounded(&full[s], ph, p.lim, abort_flag, p.err);
                     if (!__all_sync(0xffffffffu, got)) {
                         ok = false;
                         break;
