@@ -55,12 +55,19 @@ def parse():
     p.add_argument("--split-place", default="auto", choices=["auto", "prepass", "in_kernel"],
                    help="3xBF16: where FP32 operands are split into hi/lo BF16 -- library "
                         "choice, a split pass before the kernel, or inside the kernel")
+    p.add_argument("--shape", type=int, nargs=3, metavar=("M", "N", "K"),
+                   default=[128, 8192, 8192], help="--workload shape: the GEMM's M N K")
+    p.add_argument("--inputs", default="fp32", choices=["fp32", "bf16"],
+                   help="--workload shape: FP32 operands through gemm() in --mode, or BF16 "
+                        "operands through gemm_bf16")
     p.add_argument("--workload", default="square",
-                   choices=["square", "rect", "grouped", "chain", "syr2k", "sweep"],
+                   choices=["square", "rect", "grouped", "chain", "syr2k", "sweep", "shape"],
                    help="square: the 8192^3 headline; rect: BF16-input rectangular shapes; "
                         "grouped: 512 uneven problems; chain: Y = X W forward + backward; "
                         "syr2k: the rank-2k update of Section 5.1 at N = K = --size; "
-                        "sweep: sizes 1024..8192 x transposes x distributions x modes")
+                        "sweep: sizes 1024..8192 x transposes x distributions x modes; "
+                        "shape: one NN GEMM of --shape M N K (alpha 1, beta 0), e.g. for a "
+                        "profiler")
     return p.parse_args()
 
 
@@ -978,6 +985,49 @@ def run_sweep(args):
                       "cases": cases}), flush=True)
 
 
+def run_shape(args):
+    """One NN GEMM of shape M x N x K, alpha = 1, beta = 0, N(0, 1/sqrt(K))
+    operands: FP32 through gemm() in --mode (with --split-place), or BF16
+    through gemm_bf16.  Times --steps back-to-back calls after --warmup and
+    prints one JSON line (a small, self-contained case for ncu captures)."""
+    import torch
+
+    from paper_2305_18236_gb300 import build as pbuild
+
+    pbuild.build()
+    from paper_2305_18236_gb300 import gemm as g
+    from paper_2305_18236_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    M, N, K = args.shape
+    peaks, src = load_peaks()
+    A = torch.from_numpy(inputs.normal((M, K), SEED, 1.0 / K ** 0.5)).cuda()
+    B = torch.from_numpy(inputs.normal((K, N), SEED + 1, 1.0 / K ** 0.5)).cuda()
+    C = torch.empty((M, N), device="cuda")
+    h = g.Gemm()
+    h.set_config(operand_layout=args.operand_layout, split_place=args.split_place)
+    if args.inputs == "bf16":
+        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+        call = lambda: g.matmul_bf16(A, B, C=C, h=h)
+        nbytes = 2.0 * (M * K + K * N) + 4.0 * M * N
+        mode = "bf16"
+    else:
+        call = lambda: g.matmul(A, B, C=C, mode=args.mode, h=h)
+        nbytes = 4.0 * (M * K + K * N + M * N)
+        mode = args.mode
+    ms = _events_ms(call, args.steps, args.warmup, torch.cuda.current_stream())
+    if h.sync() != 0:
+        raise RuntimeError("kernel reported a bounded-wait timeout")
+    flops = 2.0 * M * N * K
+    print(json.dumps({"metric": "GEMM %dx%dx%d %s inputs, %s" % (M, N, K, args.inputs, mode),
+                      "value": flops / ms / 1e9, "unit": "TFLOP/s", "ms": ms,
+                      "gbs": nbytes / ms / 1e6, "frac_hbm": nbytes / ms / 1e6 / peaks["hbm_gbs"],
+                      "launches": h.last_launch_count(), "steps": args.steps,
+                      "warmup": args.warmup, "split_place": args.split_place,
+                      "data": "synthetic", "peaks_source": src}), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -992,6 +1042,8 @@ def main():
         run_syr2k(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "shape":
+        run_shape(args)
     else:
         run_ours(args)
 
