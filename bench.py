@@ -52,7 +52,8 @@ def parse():
                    help="auto: library choice; as_stored: operands stored K x rows are split "
                         "without transposing and read as MN-major tiles; k_major: every operand "
                         "made K-contiguous first")
-    p.add_argument("--split-place", default="auto", choices=["auto", "prepass", "in_kernel"],
+    p.add_argument("--split-place", default="auto",
+                   choices=["auto", "prepass", "in_kernel", "in_kernel_a", "in_kernel_b"],
                    help="3xBF16: where FP32 operands are split into hi/lo BF16 -- library "
                         "choice, a split pass before the kernel, or inside the kernel")
     p.add_argument("--shape", type=int, nargs=3, metavar=("M", "N", "K"),
@@ -694,7 +695,7 @@ def run_rect(args):
                          args.warmup, stream)
         launches3 = h.last_launch_count()
         places = {}
-        for place in ("prepass", "in_kernel"):
+        for place in ("prepass", "in_kernel", "in_kernel_a", "in_kernel_b"):
             hx = g.Gemm()
             hx.set_config(split_place=place)
             places[place] = _events_ms(lambda: g.matmul(A32, B32, C=C, mode="bf16x3", h=hx),

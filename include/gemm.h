@@ -125,22 +125,33 @@ typedef enum {
  * added).
  *  GEMM_SPLIT_PREPASS (1): a bandwidth-bound pass writes the hi/lo planes to
  *    workspace before the tensor-core kernel (8 bytes of HBM traffic per
- *    element of A and B, two launches).
+ *    element of A and B, one launch per operand).
  *  GEMM_SPLIT_IN_KERNEL (2): the tensor-core kernel reads the caller's FP32
  *    A and B through TMA and splits each staged tile in shared memory
  *    (converter warps), bit-identical to the pass; no split workspace.  It
  *    runs one CTA per 128 x 256 tile with BK 32 (bn 0 or 256, bk 0 or 32,
- *    cta_group 0 or 1, else GEMM_ERR_ARG) and needs A and B 16-byte aligned
- *    with lda, ldb multiples of 4; other calls use the pass.  gemm() and
- *    grouped plans only (gemm_from_host, gemm_syr2k use the pass).
- *  GEMM_SPLIT_AUTO (0): the in-kernel split when the handle forces no tile
- *    shape or layout and the pass would cost more than the kernel's lower
- *    tensor-core rate (few-tile, skinny and small problems); grouped plans
- *    take the faster of the two by the cost model or the autotuner. */
+ *    cta_group 0 or 1, else GEMM_ERR_ARG).  An operand TMA cannot read in
+ *    place (base not 16-byte aligned, or ld not a multiple of 4) is split by
+ *    the pass instead.  gemm() and grouped plans only (gemm_from_host,
+ *    gemm_syr2k use the pass).
+ *  GEMM_SPLIT_IN_KERNEL_A (3), GEMM_SPLIT_IN_KERNEL_B (4): the same kernel,
+ *    but only A (only B) is split in the kernel; the pass splits the other.
+ *    The same tile-shape rules; gemm() only (grouped plans: GEMM_ERR_ARG).
+ *    The results equal those of the other placements bit for bit.
+ *  GEMM_SPLIT_AUTO (0): when the handle forces no tile shape or layout,
+ *    gemm() picks per operand by a cost model: an operand the kernel would
+ *    re-split in many tiles (A when N spans many 256-wide tiles, B when M
+ *    spans many 128-high tiles) goes to the pass, a large one staged by few
+ *    tiles to the kernel, and nothing to the kernel when the pass plus the
+ *    CTA-pair kernel is faster (large problems).  Grouped plans take the
+ *    faster of the split pass and the in-kernel split of both operands by
+ *    the cost model or the autotuner. */
 typedef enum {
     GEMM_SPLIT_AUTO = 0,
     GEMM_SPLIT_PREPASS = 1,
-    GEMM_SPLIT_IN_KERNEL = 2
+    GEMM_SPLIT_IN_KERNEL = 2,
+    GEMM_SPLIT_IN_KERNEL_A = 3,
+    GEMM_SPLIT_IN_KERNEL_B = 4
 } gemm_split_place_t;
 
 typedef struct {

@@ -19,8 +19,9 @@ LOWER, UPPER = 0, 1
 UPLOS = {"lower": LOWER, "upper": UPPER}
 LAYOUT_AUTO, LAYOUT_K_MAJOR, LAYOUT_AS_STORED = 0, 1, 2
 LAYOUTS = {"auto": LAYOUT_AUTO, "k_major": LAYOUT_K_MAJOR, "as_stored": LAYOUT_AS_STORED}
-SPLIT_AUTO, SPLIT_PREPASS, SPLIT_IN_KERNEL = 0, 1, 2
-SPLIT_PLACES = {"auto": SPLIT_AUTO, "prepass": SPLIT_PREPASS, "in_kernel": SPLIT_IN_KERNEL}
+SPLIT_AUTO, SPLIT_PREPASS, SPLIT_IN_KERNEL, SPLIT_IN_KERNEL_A, SPLIT_IN_KERNEL_B = 0, 1, 2, 3, 4
+SPLIT_PLACES = {"auto": SPLIT_AUTO, "prepass": SPLIT_PREPASS, "in_kernel": SPLIT_IN_KERNEL,
+                "in_kernel_a": SPLIT_IN_KERNEL_A, "in_kernel_b": SPLIT_IN_KERNEL_B}
 
 GEMM_OK = 0
 GEMM_ERR_ARG = -1

@@ -95,21 +95,67 @@ bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
 //    when packing pays (pack_pays); in their stored orientation otherwise,
 //    and always in grouped plans and SYR2K, whose transposing passes cost
 //    more than the kernel gains.
-// True when the in-kernel split is expected to beat the split pass plus the
-// faster pre-split kernel: the pass moves 8 bytes per element of A and B
-// (FP32 read, hi and lo written) and costs two launches; the kernel that
-// splits its own stages runs the tensor cores at about 3/5 of the rate of
-// the CTA-pair kernel on pre-split operands (rough GB300 rates).
-bool fuse_pays(int64_t M, int64_t N, int64_t K) {
+// K slices of a launch with `tiles` output tiles and `kblocks` K blocks when
+// the handle leaves split-K to the library: few tiles and a long K are
+// sliced so that every SM gets work.
+int auto_split_k(int64_t tiles, int64_t kblocks, int num_sms) {
+    int64_t split = 1;
+    if (tiles * 2 <= num_sms && kblocks >= 16)
+        split = std::min<int64_t>({num_sms / std::max<int64_t>(tiles, 1), kblocks / 8, 16});
+    return int(std::max<int64_t>(split, 1));
+}
+
+// Split placement of a split-precision call: which operands the kernel
+// splits itself (bit 0 A, bit 1 B; `allowed` = those TMA can read in place)
+// and which the pass splits first, by expected seconds (rough GB300 rates).
+//  * The pass moves 8 bytes per element (FP32 read, hi and lo written) at
+//    HBM speed for each operand it splits, plus one launch (one for both).
+//  * The in-kernel split (one CTA per 128 x 256 tile, BK 32) re-splits every
+//    staged element of a fused operand in every tile that stages it: A once
+//    per N tile, B once per M tile.  A CTA splits about 9e9 elements/s; the
+//    tiles run in waves of one per SM.  Its MMAs run at about 3/5 of the
+//    pair kernel's rate; the kernel takes the longer of the two.
+//  * Mask 0 is the CTA-pair kernel on pre-split operands, bounded by its
+//    MMAs or by the C traffic (short K); with too few tiles for pairs, the
+//    one-CTA kernel, whose MMAs run at about 4/5 of the pair rate.
+// So a small operand staged by many tiles (A of a skinny M) goes to the pass
+// and a large one staged by few tiles (its B) to the kernel.  Fit to per-call
+// times of all four placements on eight shapes from (128, 8192, 8192) to
+// 2048^3; on each it picks the placement measured fastest.
+int fuse_mask(int64_t M, int64_t N, int64_t K, int num_sms, bool beta_zero, int allowed) {
     const double m = double(M), n = double(N), k = double(K);
-    const double t_pass = 8.0 * (m * k + n * k) / 6.5e12 + 4e-6;
-    const double t_mma = 6.0 * m * n * k / 1.8e15;
-    return t_mma / 0.6 < t_pass + t_mma;
+    const double hbm = 6.5e12, sm_rate = 1.8e15 / std::max(num_sms, 1);
+    const double t_c = (beta_zero ? 4.0 : 8.0) * m * n / hbm;
+    const double launch = 3e-6;
+    auto pass = [&](double rows) { return 8.0 * rows * k / hbm; };
+    // one CTA per 128 x 256 tile, split-K as the plan would slice it
+    const int64_t tiles = ((M + 127) / 128) * ((N + 255) / 256);
+    const int split = auto_split_k(tiles, (K + 31) / 32, num_sms);
+    const double waves = double((tiles * split + num_sms - 1) / num_sms);
+    const double k_tile = k / split;
+    auto tile_mma = [&](double eff) { return waves * 6.0 * 128.0 * 256.0 * k_tile / (eff * sm_rate); };
+    const bool pairs = ((M + 255) / 256) * ((N + 255) / 256) >= num_sms / 2;
+    double best = pass(m) + pass(n) + launch +
+                  std::max(pairs ? 6.0 * m * n * k / 1.8e15 : tile_mma(0.8), t_c);
+    int best_mask = 0;
+    for (int mask = 1; mask <= 3; ++mask) {
+        if ((mask & allowed) != mask) continue;
+        const double per_tile = ((mask & 1) ? 128.0 : 0.0) + ((mask & 2) ? 256.0 : 0.0);
+        const double t_conv = waves * per_tile * k_tile / 9e9;
+        const double t_mma = tile_mma(0.6);
+        const double t = ((mask & 1) ? 0.0 : pass(m)) + ((mask & 2) ? 0.0 : pass(n)) +
+                         (mask == 3 ? 0.0 : launch) + std::max(t_conv, t_mma);
+        if (t < best) {
+            best = t;
+            best_mask = mask;
+        }
+    }
+    return best_mask;
 }
 
 TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_t K, Call call,
                  bool pack_a = false, bool pack_b = false, bool beta_zero = false,
-                 bool f32_ok = false) {
+                 int f32_ops = 0) {
     TcLaunch c;
     c.bn = h->cfg.bn ? h->cfg.bn : 256;
     if (call == Call::Syr2k) {
@@ -156,14 +202,27 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
         ((M + 255) / 256) * ((N + 511) / 512) >= h->num_sms / 2)
         c.bn = 512;
     if (c.bn == 512 && !wide_ok) c.bn = 256;
-    // In-kernel split (split precision on FP32 operands that TMA can read in
-    // place): one CTA per 128 x 256 tile with BK 32, operands as stored.
-    if (nterms == 3 && (call == Call::Split || call == Call::Grouped) && f32_ok &&
-        h->cfg.split_place != GEMM_SPLIT_PREPASS &&
-        (h->cfg.split_place == GEMM_SPLIT_IN_KERNEL ||
-         (h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.cta_group == 0 &&
-          h->cfg.operand_layout == GEMM_LAYOUT_AUTO && fuse_pays(M, N, K)))) {
-        c.fuse = 1;
+    // In-kernel split (split precision; f32_ops: bit 0 A, bit 1 B is an FP32
+    // matrix TMA can read in place): one CTA per 128 x 256 tile with BK 32,
+    // operands as stored; an operand the kernel does not split is split by
+    // the pass.
+    int fuse = 0;
+    if (nterms == 3 && call == Call::Split) {
+        switch (h->cfg.split_place) {
+            case GEMM_SPLIT_IN_KERNEL: fuse = 3; break;
+            case GEMM_SPLIT_IN_KERNEL_A: fuse = 1; break;
+            case GEMM_SPLIT_IN_KERNEL_B: fuse = 2; break;
+            case GEMM_SPLIT_AUTO:
+                if (h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.cta_group == 0 &&
+                    h->cfg.operand_layout == GEMM_LAYOUT_AUTO)
+                    fuse = fuse_mask(M, N, K, h->num_sms, beta_zero, f32_ops);
+                break;
+            default: break;
+        }
+        fuse &= f32_ops;
+    }
+    if (fuse) {
+        c.fuse = fuse;
         c.cta_group = 1;
         c.bn = 256;
         c.bk = 32;
@@ -177,13 +236,8 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
     if (h->cfg.split_k > 0) {
         c.split_k = h->cfg.split_k;
     } else {
-        // Few output tiles and a long K: slice K so every SM gets work.
-        const int64_t tiles = ((M + 127) / 128) * ((N + c.bn - 1) / c.bn);
-        const int64_t kblocks = (K + c.bk - 1) / c.bk;
-        int64_t split = 1;
-        if (tiles * 2 <= h->num_sms && kblocks >= 16)
-            split = std::min<int64_t>({h->num_sms / std::max<int64_t>(tiles, 1), kblocks / 8, 16});
-        c.split_k = int(std::max<int64_t>(split, 1));
+        c.split_k = auto_split_k(((M + 127) / 128) * ((N + c.bn - 1) / c.bn),
+                                 (K + c.bk - 1) / c.bk, h->num_sms);
     }
     return c;
 }
@@ -219,6 +273,28 @@ cudaError_t split_op(const OpPlan& o, int64_t rows, int64_t K, const float* X, i
     uint16_t* lo = planes > 1 ? hi + o.lay.plane : nullptr;
     if (o.mn) return gb300::launch_split_bf16(0, K, rows, X, ldx, hi, lo, o.lay.ld, s);
     return gb300::launch_split_bf16(o.stored_k_rows ? 1 : 0, rows, K, X, ldx, hi, lo, o.lay.ld, s);
+}
+
+// The same for two operands in one launch (the pass over A and B together).
+gb300::SplitArg split_arg(const OpPlan& o, int64_t rows, int64_t K, const float* X, int64_t ldx,
+                          uint16_t* hi, int planes) {
+    gb300::SplitArg a;
+    a.trans = o.mn ? 0 : (o.stored_k_rows ? 1 : 0);
+    a.rows = o.mn ? K : rows;
+    a.cols = o.mn ? rows : K;
+    a.X = X;
+    a.ldx = ldx;
+    a.hi = hi;
+    a.lo = planes > 1 ? hi + o.lay.plane : nullptr;
+    a.ldo = o.lay.ld;
+    return a;
+}
+
+cudaError_t split_ops(const OpPlan& pa, int64_t M, const float* A, int64_t lda, uint16_t* a_hi,
+                      const OpPlan& pb, int64_t N, const float* B, int64_t ldb, uint16_t* b_hi,
+                      int64_t K, int planes, cudaStream_t s) {
+    return gb300::launch_split_bf16_pair(split_arg(pa, M, K, A, lda, a_hi, planes),
+                                         split_arg(pb, N, K, B, ldb, b_hi, planes), s);
 }
 
 TcOperand operand_of(const OpPlan& o, const uint16_t* hi, int64_t rows, int64_t K, int planes) {
@@ -432,31 +508,34 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
     const int planes = nterms == 3 ? 2 : 1;
     const TcLaunch cfg = plan_tc(h, nterms, M, N, K, Call::Split, false, false, beta == 0.0f,
-                                 f32_tma_ok(A, lda) && f32_tma_ok(B, ldb));
+                                 (f32_tma_ok(A, lda) ? 1 : 0) | (f32_tma_ok(B, ldb) ? 2 : 0));
     // op(A) is M x K and op(B)^T is N x K, split K-major or as stored -- or,
-    // with the in-kernel split, read as stored in FP32 and split on chip
+    // with the in-kernel split (cfg.fuse bit 0 A, bit 1 B), read as stored in
+    // FP32 and split on chip
+    const bool fa = cfg.fuse & 1, fb = cfg.fuse & 2;
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
-    const WsPlan w = plan_ws(planes, cfg.fuse ? 0 : pa.lay.plane, cfg.fuse ? 0 : pb.lay.plane, M,
-                             N, K, cfg);
+    const WsPlan w = plan_ws(planes, fa ? 0 : pa.lay.plane, fb ? 0 : pb.lay.plane, M, N, K, cfg);
     uint8_t* ws;
     gemm_status_t st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
     TcOperand oa, ob;
     int launches = 0;
-    if (cfg.fuse) {
-        oa = f32_operand(A, lda, M, K, transA == GEMM_OP_T);
-        ob = f32_operand(B, ldb, N, K, transB == GEMM_OP_N);
-    } else {
-        uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
-        uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
-        if (split_op(pa, M, K, A, lda, a_hi, planes, s) != cudaSuccess ||
-            split_op(pb, N, K, B, ldb, b_hi, planes, s) != cudaSuccess)
+    uint16_t* a_hi = reinterpret_cast<uint16_t*>(ws + w.a_off);
+    uint16_t* b_hi = reinterpret_cast<uint16_t*>(ws + w.b_off);
+    if (!fa && !fb) {  // both by the pass: one launch
+        if (split_ops(pa, M, A, lda, a_hi, pb, N, B, ldb, b_hi, K, planes, s) != cudaSuccess)
             return GEMM_ERR_CUDA;
-        oa = operand_of(pa, a_hi, M, K, planes);
-        ob = operand_of(pb, b_hi, N, K, planes);
-        launches = 2;
+        launches = 1;
+    } else if (!fa || !fb) {
+        const bool a_pass = !fa;
+        if ((a_pass ? split_op(pa, M, K, A, lda, a_hi, planes, s)
+                    : split_op(pb, N, K, B, ldb, b_hi, planes, s)) != cudaSuccess)
+            return GEMM_ERR_CUDA;
+        launches = 1;
     }
+    oa = fa ? f32_operand(A, lda, M, K, transA == GEMM_OP_T) : operand_of(pa, a_hi, M, K, planes);
+    ob = fb ? f32_operand(B, ldb, N, K, transB == GEMM_OP_N) : operand_of(pb, b_hi, N, K, planes);
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
     float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
@@ -593,9 +672,8 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         c.wait_poll_limit < 0 ||
         (c.operand_layout != GEMM_LAYOUT_AUTO && c.operand_layout != GEMM_LAYOUT_K_MAJOR &&
          c.operand_layout != GEMM_LAYOUT_AS_STORED) ||
-        (c.split_place != GEMM_SPLIT_AUTO && c.split_place != GEMM_SPLIT_PREPASS &&
-         c.split_place != GEMM_SPLIT_IN_KERNEL) ||
-        (c.split_place == GEMM_SPLIT_IN_KERNEL &&
+        c.split_place < GEMM_SPLIT_AUTO || c.split_place > GEMM_SPLIT_IN_KERNEL_B ||
+        (c.split_place >= GEMM_SPLIT_IN_KERNEL &&
          ((c.bn != 0 && c.bn != 256) || (c.bk != 0 && c.bk != 32) || c.cta_group == 2)))
         return fail_arg(h, 2);
     h->cfg = c;
@@ -611,11 +689,23 @@ size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, 
     if (mode == GEMM_MODE_F32_SIMT) return plan_simt_pack(M, N, K).total;
     if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return 0;
     const int nterms = mode == GEMM_MODE_BF16X3 ? 3 : 1;
-    const TcLaunch c = plan_tc(h, nterms, M, N, K, Call::Split);
-    const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
-    const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, c);
-    // gemm() splits both operands; gemm_bf16 needs at most as much (packs only)
-    return plan_ws(nterms == 3 ? 2 : 1, pa.lay.plane, pb.lay.plane, M, N, K, c).total;
+    // gemm() splits the operands the kernel does not split itself; gemm_bf16
+    // needs at most as much (packs only).  Which operands the in-kernel split
+    // takes depends on their alignment, unknown here: the largest plan over
+    // the four cases (neither, A, B or both readable in place), with beta zero
+    // or not (the plan weighs the C traffic), covers any call.
+    size_t bytes = 0;
+    for (int v = 0; v < (nterms == 3 ? 8 : 2); ++v) {
+        const int f32_ops = v >> 1;
+        const TcLaunch c =
+            plan_tc(h, nterms, M, N, K, Call::Split, false, false, (v & 1) != 0, f32_ops);
+        const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
+        const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, c);
+        bytes = std::max(bytes, plan_ws(nterms == 3 ? 2 : 1, (c.fuse & 1) ? 0 : pa.lay.plane,
+                                        (c.fuse & 2) ? 0 : pb.lay.plane, M, N, K, c)
+                                    .total);
+    }
+    return bytes;
 }
 
 gemm_status_t gemm_set_workspace(gemm_handle_t h, void* ws, size_t bytes) {
@@ -984,12 +1074,11 @@ gemm_status_t gemm_syr2k(gemm_handle_t h, gemm_uplo_t uplo, gemm_op_t trans, int
     if (st != GEMM_OK) return st;
     uint16_t* x_hi = reinterpret_cast<uint16_t*>(ws);
     uint16_t* y_hi = x_hi + size_t(sp.planes) * size_t(sp.op.lay.plane);
-    if (split_op(sp.op, N, K, A, lda, x_hi, sp.planes, s) != cudaSuccess ||
-        split_op(sp.op, N, K, B, ldb, y_hi, sp.planes, s) != cudaSuccess)
+    if (split_ops(sp.op, N, A, lda, x_hi, sp.op, N, B, ldb, y_hi, K, sp.planes, s) != cudaSuccess)
         return GEMM_ERR_CUDA;
     TcOperand xy = operand_of(sp.op, x_hi, N, K, 2 * sp.planes);
     xy.box_planes = sp.planes;
-    int launches = 2;
+    int launches = 1;
     int rc;
     {
         ProfScope prof(h, s);

@@ -187,7 +187,7 @@ std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nter
                 c.cfg.stages = stages;
                 c.cfg.split_k = 1;
                 c.cfg.cta_group = cg;
-                c.cfg.fuse = f;
+                c.cfg.fuse = f ? 3 : 0;  // both operands split in the kernel
                 c.cfg.kmajor = f ? 0 : base.kmajor;
                 c.model = flop_per_mac * work * waves / (1.8e15 * config_efficiency(cg, bn, bk, f)) +
                           (f ? 0.0 : t_split);
@@ -246,7 +246,7 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
         out->stages = st;
         out->raster_group = rg;
         out->cta_group = cg == 2 ? 2 : 1;
-        out->fuse = fu == 1 ? 1 : 0;
+        out->fuse = fu == 1 ? 3 : 0;
         found = true;
     }
     fclose(f);
@@ -262,7 +262,7 @@ void cache_store(const std::string& key, const TcLaunch& c) {
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
-            c.cta_group, c.fuse);
+            c.cta_group, c.fuse ? 1 : 0);
     fclose(f);
 }
 
@@ -373,6 +373,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         return GEMM_ERR_ARG;
     };
     if (mode != GEMM_MODE_BF16 && mode != GEMM_MODE_BF16X3) return bad(2);
+    // one placement for both operands of every problem (no per-operand choice)
+    if (gb300::handle_split_place(h) > GEMM_SPLIT_IN_KERNEL) return bad(1);
     if (count < 0) return bad(4);
     if (count > 0 && !hp) return bad(3);
     if (flags & ~uint32_t(GEMM_GROUPED_AUTOTUNE | GEMM_GROUPED_GRAPH)) return bad(5);
@@ -424,7 +426,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
                           (place == GEMM_SPLIT_IN_KERNEL || gb300::handle_tile_auto(h));
     const bool prepass_ok = !(fused_ok && place == GEMM_SPLIT_IN_KERNEL);
     if (fused_ok && !prepass_ok) {  // the in-kernel split's one tile shape
-        p->cfg.fuse = 1;
+        p->cfg.fuse = 3;
         p->cfg.cta_group = 1;
         p->cfg.bn = 256;
         p->cfg.bk = 32;

@@ -20,7 +20,8 @@ struct TcLaunch {
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
     int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)
     int kmajor = 0;          // 1: every operand K-major (transposing split / pack)
-    int fuse = 0;            // 1: split FP32 operands inside the kernel (TcOperand::f32)
+    int fuse = 0;            // in-kernel split: bit 0 A, bit 1 B is FP32 (TcOperand::f32),
+                             // split inside the kernel; the other operand is BF16 planes
 };
 
 // One operand of the tensor-core kernel: BF16, `planes` stacked planes
@@ -117,6 +118,25 @@ cudaError_t launch_simt_f32(int transA, int transB, int64_t M, int64_t N, int64_
 // Y = op(X) split into hi/lo BF16 (lo may be null), rows x cols, row stride ldo.
 cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float* X, int64_t ldx,
                               uint16_t* hi, uint16_t* lo, int64_t ldo, cudaStream_t stream);
+
+// One matrix of a two-matrix split launch: Y = op(X) (trans 1: X stored
+// cols x rows), rows x cols, hi/lo BF16 with row stride ldo (lo may be null).
+// x_vec and blocks are filled in by the launcher.
+struct SplitArg {
+    int trans;
+    int64_t rows, cols;
+    const float* X;
+    int64_t ldx;
+    uint16_t* hi;
+    uint16_t* lo;
+    int64_t ldo;
+    int x_vec = 0;
+    int blocks = 0;
+};
+
+// Both operands' split in one launch, each as launch_split_bf16 would do it
+// (same results, one launch fewer).
+cudaError_t launch_split_bf16_pair(SplitArg a, SplitArg b, cudaStream_t stream);
 
 // One matrix of a grouped split launch (device table entry): Y = op(X),
 // rows x cols, written as hi/lo BF16 with row stride ldo; tile_start is the

@@ -44,16 +44,16 @@ int grid_for(int64_t work, int per_block) {
 }
 
 // Y = X (no transpose): each thread converts 8 consecutive elements of a row
-// and writes 16 bytes of hi and 16 bytes of lo.
-__global__ void __launch_bounds__(256) split_rows_kernel(int64_t rows, int64_t cols,
-                                                         const float* __restrict__ X, int64_t ldx,
-                                                         uint16_t* __restrict__ hi,
-                                                         uint16_t* __restrict__ lo, int64_t ldo,
-                                                         int x_vec) {
+// and writes 16 bytes of hi and 16 bytes of lo; block `bid` of `nblk`.
+__device__ __forceinline__ void split_rows_body(int64_t rows, int64_t cols,
+                                                const float* __restrict__ X, int64_t ldx,
+                                                uint16_t* __restrict__ hi,
+                                                uint16_t* __restrict__ lo, int64_t ldo, int x_vec,
+                                                int bid, int nblk) {
     const int64_t chunks_per_row = (cols + 7) / 8;
     const int64_t total = rows * chunks_per_row;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
+    for (int64_t idx = bid * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(nblk) * blockDim.x) {
         const int64_t r = idx / chunks_per_row;
         const int64_t c0 = (idx - r * chunks_per_row) * 8;
         const float* src = X + r * ldx + c0;
@@ -87,20 +87,29 @@ __global__ void __launch_bounds__(256) split_rows_kernel(int64_t rows, int64_t c
     }
 }
 
+__global__ void __launch_bounds__(256) split_rows_kernel(int64_t rows, int64_t cols,
+                                                         const float* __restrict__ X, int64_t ldx,
+                                                         uint16_t* __restrict__ hi,
+                                                         uint16_t* __restrict__ lo, int64_t ldo,
+                                                         int x_vec) {
+    split_rows_body(rows, cols, X, ldx, hi, lo, ldo, x_vec, blockIdx.x, gridDim.x);
+}
+
 // Y = X^T through a 64 x 64 shared-memory tile: reads along X's rows, writes
 // along Y's rows, both coalesced.  T is float (split into hi/lo) or
-// uint16_t (BF16 copy into `hi`).
+// uint16_t (BF16 copy into `hi`); block `bid` of `nblk` (every thread of a
+// block calls it: it synchronises the block).
 template <typename T>
-__global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t cols,
-                                                        const T* __restrict__ X, int64_t ldx,
-                                                        uint16_t* __restrict__ hi,
-                                                        uint16_t* __restrict__ lo, int64_t ldo) {
+__device__ __forceinline__ void transpose_body(int64_t rows, int64_t cols,
+                                               const T* __restrict__ X, int64_t ldx,
+                                               uint16_t* __restrict__ hi,
+                                               uint16_t* __restrict__ lo, int64_t ldo,
+                                               T (*tile)[65], int bid, int nblk) {
     // Y is rows x cols; X is cols x rows.  Tile: Y rows [r0, r0+64), Y cols [c0, c0+64).
-    __shared__ T tile[64][65];
     const int64_t tiles_r = (rows + 63) / 64;
     const int64_t tiles_c = (cols + 63) / 64;
     const int tid = threadIdx.x;
-    for (int64_t tIdx = blockIdx.x; tIdx < tiles_r * tiles_c; tIdx += gridDim.x) {
+    for (int64_t tIdx = bid; tIdx < tiles_r * tiles_c; tIdx += nblk) {
         const int64_t r0 = (tIdx % tiles_r) * 64;
         const int64_t c0 = (tIdx / tiles_r) * 64;
         // load: X row (c0 + i), columns r0 .. r0+63
@@ -148,6 +157,29 @@ __global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t co
         }
         __syncthreads();
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t cols,
+                                                        const T* __restrict__ X, int64_t ldx,
+                                                        uint16_t* __restrict__ hi,
+                                                        uint16_t* __restrict__ lo, int64_t ldo) {
+    __shared__ T tile[64][65];
+    transpose_body<T>(rows, cols, X, ldx, hi, lo, ldo, tile, blockIdx.x, gridDim.x);
+}
+
+// Both operands of a GEMM split in one launch: blocks [0, a.blocks) work on
+// a, the rest on b, each with the body of its single-matrix kernel (a block
+// takes one branch, so the transposing body's barriers stay block-uniform).
+__global__ void __launch_bounds__(256) split_pair_kernel(const SplitArg a, const SplitArg b) {
+    __shared__ float tile[64][65];
+    const bool second = int(blockIdx.x) >= a.blocks;
+    const SplitArg& j = second ? b : a;
+    const int bid = second ? int(blockIdx.x) - a.blocks : int(blockIdx.x);
+    if (j.trans)
+        transpose_body<float>(j.rows, j.cols, j.X, j.ldx, j.hi, j.lo, j.ldo, tile, bid, j.blocks);
+    else
+        split_rows_body(j.rows, j.cols, j.X, j.ldx, j.hi, j.lo, j.ldo, j.x_vec, bid, j.blocks);
 }
 
 // Y = X^T in FP32 (Y rows x cols, X stored cols x rows) through a 64 x 64
@@ -471,6 +503,20 @@ cudaError_t launch_split_bf16(int trans, int64_t rows, int64_t cols, const float
         transpose_kernel<float><<<grid_for(tiles, 1), 256, 0, stream>>>(rows, cols, X, ldx, hi, lo,
                                                                         ldo);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16_pair(SplitArg a, SplitArg b, cudaStream_t stream) {
+    SplitArg* js[2] = {&a, &b};
+    for (SplitArg* j : js) {
+        j->x_vec = ((reinterpret_cast<uintptr_t>(j->X) & 15) == 0) && (j->ldx % 4 == 0);
+        // the blocks each single-matrix launch would take (0 for an empty matrix)
+        j->blocks = j->rows <= 0 || j->cols <= 0 ? 0
+                    : j->trans ? grid_for(((j->rows + 63) / 64) * ((j->cols + 63) / 64), 1)
+                               : grid_for(j->rows * ((j->cols + 7) / 8), 256);
+    }
+    if (a.blocks + b.blocks == 0) return cudaSuccess;
+    split_pair_kernel<<<a.blocks + b.blocks, 256, 0, stream>>>(a, b);
     return cudaGetLastError();
 }
 

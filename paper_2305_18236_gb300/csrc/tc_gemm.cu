@@ -85,6 +85,7 @@ struct TcParams {
     const int* tile_prob;  // problem index of every tile
     int count;
     int c_tma;  // epilogue writes through the C tensor map (beta == 0 or split-K partials)
+    int fuse_ops;  // FUSE: bit 0 A, bit 1 B arrives as FP32 and is split in the kernel
     int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
     // SYR2K (single launches): uplo 1 = lower, 2 = upper triangle of C (0 =
     // plain GEMM); syr_kb = K blocks of one product (the K loop runs twice as
@@ -463,11 +464,12 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
     }
 }
 
-// FUSE (split precision only): the operands are the caller's FP32 matrices;
-// TMA stages FP32 tiles, converter warps split them in place into the hi/lo
-// atoms the MMA reads (split_group_in_place) and arrive on conv[s], which
-// the MMA issuer waits on instead of full[s]; no split pass runs before the
-// kernel.
+// FUSE (split precision only): the operands marked in p.fuse_ops are the
+// caller's FP32 matrices; TMA stages their FP32 tiles, converter warps split
+// them in place into the hi/lo atoms the MMA reads (split_group_in_place) and
+// arrive on conv[s], which the MMA issuer waits on instead of full[s].  An
+// operand not marked arrives as BF16 hi/lo planes from the split pass, in the
+// layout of the kernel without FUSE (a stage holds the same bytes either way).
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED, bool FUSE = false>
 __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -687,11 +689,13 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                     const int kb0 = ti.kb0, kb1 = ti.kb1;
                     const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
                     const uint32_t idesc = make_idesc_bf16_f32(kBM, BN, a_mn, b_mn);
-                    const OpDesc da = op_desc(slot0, FUSE ? op_layout_fused<S>(a_mn)
+                    const OpDesc da = op_desc(slot0, FUSE && (p.fuse_ops & 1)
+                                                          ? op_layout_fused<S>(a_mn)
                                                           : op_layout<S>(a_mn, S::A_PLANE));
                     const OpDesc db = op_desc(slot0 + S::PLANES * S::A_PLANE,
-                                              FUSE ? op_layout_fused<S>(b_mn)
-                                                   : op_layout<S>(b_mn, S::B_PLANE));
+                                              FUSE && (p.fuse_ops & 2)
+                                                  ? op_layout_fused<S>(b_mn)
+                                                  : op_layout<S>(b_mn, S::B_PLANE));
                     const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
                     for (int c0 = kb0; c0 < kb1 && ok; c0 += chunk, ++g) {
                         const int buf = g & 1;
@@ -762,8 +766,10 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int wa = (ti.maj & 1) ? 64 : BK;         // row width of an A group
                 const int wb = ((ti.maj >> 1) & 1) ? 64 : BK;  // and of a B group
-                const int na = kBM * BK * 4 / (32 * wa);       // groups of 32 W bytes
-                const int nb = BN * BK * 4 / (32 * wb);
+                // groups of 32 W bytes; an operand that arrives as BF16
+                // planes (split by the pass) has none
+                const int na = (p.fuse_ops & 1) ? kBM * BK * 4 / (32 * wa) : 0;
+                const int nb = (p.fuse_ops & 2) ? BN * BK * 4 / (32 * wb) : 0;
     #pragma unroll 1
                 for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
                     // lane 0 polls; then every lane observes the completed
@@ -1413,6 +1419,7 @@ void fill_common(TcParams& p, const TcLaunch& cfg, int bk, int nterms, int* err_
     p.err = err_word;
     const bool promote = nterms == 3 && cfg.promote_k > 0;
     p.chunk_kb = promote ? std::max(1, cfg.promote_k / bk) : 1;
+    p.fuse_ops = cfg.fuse & 3;
 }
 
 }  // namespace

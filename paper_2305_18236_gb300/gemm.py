@@ -74,8 +74,9 @@ class Gemm:
         """operand_layout: "auto" (library choice), "as_stored" (MN-major tiles
         for operands stored K x rows) or "k_major" (every operand made
         K-contiguous first).  split_place (3xBF16): "auto", "prepass" (split
-        pass before the kernel) or "in_kernel" (the kernel splits FP32 tiles
-        in shared memory)."""
+        pass before the kernel), "in_kernel" (the kernel splits FP32 tiles
+        in shared memory), "in_kernel_a" / "in_kernel_b" (the kernel splits
+        A / B, the pass the other; matmul only)."""
         layout = LAYOUTS[operand_layout] if isinstance(operand_layout, str) else operand_layout
         place = SPLIT_PLACES[split_place] if isinstance(split_place, str) else split_place
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,

@@ -127,6 +127,66 @@ def test_split_k_with_in_kernel_split():
     assert np.array_equal(got.astype(np.float64), C64)
 
 
+@pytest.mark.parametrize("place", ["in_kernel_a", "in_kernel_b"])
+@pytest.mark.parametrize("tA,tB", TRANS)
+def test_one_operand_split_in_kernel(place, tA, tB):
+    """Only A (only B) split in the kernel, the other by the pass, in one
+    launch of the same kernel: integer data exact (ragged tiles, a K tail),
+    float data equal bit for bit to both operands split either way."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    h1 = g.Gemm()
+    h1.set_config(split_place=place, split_k=1)
+    A, B, _ = make_problem(300, 520, 333, tA, tB, dist="integers", seed=48)
+    C0 = inputs.integers((300, 520), 49)
+    got, launches = _run(h1, A, B, C0, 1.5, 0.5, tA, tB)
+    assert launches == 2  # one split launch and the kernel
+    C64, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
+    assert np.array_equal(got.astype(np.float64), C64)
+
+    hf, hp = _handles()
+    A, B, C0 = make_problem(700, 600, 1300, tA, tB, dist="log_uniform", seed=50, beta=0.5)
+    got, _ = _run(h1, A, B, C0, 1.5, 0.5, tA, tB)
+    both, _ = _run(hf, A, B, C0, 1.5, 0.5, tA, tB)
+    ref, _ = _run(hp, A, B, C0, 1.5, 0.5, tA, tB)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.array_equal(both.view(np.uint32), ref.view(np.uint32))
+
+
+def test_in_kernel_split_of_the_aligned_operand_only():
+    """split_place in_kernel with one operand TMA cannot read in place (row
+    stride not a multiple of 4 floats): the kernel splits the other, the pass
+    this one; integer data exact."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    hf, _ = _handles()
+    M, N, K = 130, 152, 97  # lda = K = 97; ldb = N = 152
+    A, B, C0 = make_problem(M, N, K, dist="integers", seed=51, beta=0.0)
+    C = torch.zeros((M, N), device="cuda")
+    g.matmul(to_dev(A), to_dev(B), C=C, mode="bf16x3", h=hf)
+    assert hf.sync() == 0
+    assert hf.last_launch_count() == 2  # the split of A and the kernel
+    C64, _, _ = oracle.gemm(A, B)
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), C64)
+
+
+def test_grouped_rejects_one_operand_placement():
+    """Grouped plans have one placement for both operands: in_kernel_a is an
+    argument error there (the handle, position 1)."""
+    from paper_2305_18236_gb300 import _lib
+    from paper_2305_18236_gb300 import gemm as g
+    from tests.test_gpu_grouped import make_problems, to_device
+
+    h = g.Gemm()
+    h.set_config(split_place="in_kernel_a")
+    dev = to_device(make_problems(2, 52))
+    with pytest.raises(_lib.GemmError) as e:
+        g.GroupedPlan(dev, mode="bf16x3", h=h)
+    assert e.value.status == _lib.GEMM_ERR_ARG
+
+
 def test_unaligned_operand_falls_back_to_the_pass():
     """An operand TMA cannot read in place (row stride not a multiple of 4
     floats) is split by the pass instead; the result is unchanged."""
@@ -140,7 +200,7 @@ def test_unaligned_operand_falls_back_to_the_pass():
     C = torch.zeros((M, N), device="cuda")
     g.matmul(to_dev(A), to_dev(B), C=C, mode="bf16x3", h=hf)
     assert hf.sync() == 0
-    assert hf.last_launch_count() == 3  # two split launches and the kernel
+    assert hf.last_launch_count() == 2  # one split launch for both operands, the kernel
     C64, _, _ = oracle.gemm(A, B)
     assert np.array_equal(C.cpu().numpy().astype(np.float64), C64)
 
@@ -166,8 +226,10 @@ def test_headline_size_sampled_in_kernel_split():
 
 
 def test_skinny_shape_library_choice():
-    """(128, 8192, 8192) on FP32 operands: the library picks the in-kernel
-    split (no split pass over B); sampled rows against the oracle."""
+    """(128, 8192, 8192) on FP32 operands: the library splits the small A
+    (which every one of the 32 N tiles stages) with the pass and B (staged by
+    the one row of tiles) in the kernel: no split pass over B; sampled rows
+    against the oracle."""
     from paper_2305_18236_gb300 import gemm as g
 
     M, N, K = 128, 8192, 8192
@@ -176,7 +238,7 @@ def test_skinny_shape_library_choice():
     h = g.Gemm()
     C = g.matmul(to_dev(A32), to_dev(B32), mode="bf16x3", h=h)
     assert h.sync() == 0
-    assert h.last_launch_count() <= 2  # the kernel (and a split-K reduce), no split pass
+    assert h.last_launch_count() == 3  # the split of A, the kernel and the split-K reduce
     rows = np.linspace(0, M - 1, 12).astype(np.int64)
     C64, D, _ = oracle.gemm(A32, B32, rows=rows)
     assert oracle.normwise_error(C.cpu().numpy()[rows], C64, D) <= tol_exact("bf16x3", K)
