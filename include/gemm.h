@@ -82,7 +82,9 @@ typedef struct gemm_context *gemm_handle_t;
  *             bn 512 with cta_group 1 or bk 32 is GEMM_ERR_ARG.
  *  bk:        K depth of one pipeline stage (32 or 64 BF16 elements).
  *  stages:    shared-memory ring depth (2..8; clamped to what fits).
- *  split_k:   number of K slices reduced by a second kernel (1 = none).
+ *  split_k:   number of K slices (1 = none), each a partial sum; the partial
+ *             sums are added in slice order, then C = alpha * sum + beta * C,
+ *             as splitk_reduce says.
  *  raster_group: number of M tiles walked together before moving along N.
  *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).
  *  promote_k: GEMM_MODE_BF16X3 only: K elements summed in tensor memory
@@ -113,7 +115,14 @@ typedef struct gemm_context *gemm_handle_t;
  *    K-major kernel is a few percent faster and the split transposes at
  *    nearly the copy rate), as stored in grouped plans and gemm_syr2k, and
  *    in gemm_bf16 K-major only when the pack pass costs under a tenth of the
- *    GEMM (large, compute-bound shapes) -- as stored otherwise. */
+ *    GEMM (large, compute-bound shapes) -- as stored otherwise.
+ *  splitk_reduce: GEMM_SPLITK_AUTO (0): with one CTA per tile, at most 8
+ *    slices and no more (tile, slice) pairs than SMs, the slices of a tile
+ *    run as one cluster of CTAs and the GEMM kernel itself adds them after a
+ *    cluster barrier (no second launch; if such a cluster cannot be
+ *    resident the reduce launch is used); otherwise a second kernel adds
+ *    them.  GEMM_SPLITK_LAUNCH (1): always
+ *    the second kernel.  Both give the same bits. */
 typedef enum {
     GEMM_LAYOUT_AUTO = 0,
     GEMM_LAYOUT_K_MAJOR = 1,
@@ -154,6 +163,11 @@ typedef enum {
     GEMM_SPLIT_IN_KERNEL_B = 4
 } gemm_split_place_t;
 
+typedef enum {
+    GEMM_SPLITK_AUTO = 0,
+    GEMM_SPLITK_LAUNCH = 1
+} gemm_splitk_reduce_t;
+
 typedef struct {
     int32_t bn;
     int32_t bk;
@@ -165,7 +179,8 @@ typedef struct {
     int32_t cta_group;
     int64_t wait_poll_limit;
     int32_t operand_layout;
-    int32_t split_place; /* gemm_split_place_t */
+    int32_t split_place;   /* gemm_split_place_t */
+    int32_t splitk_reduce; /* gemm_splitk_reduce_t */
 } gemm_config_t;
 
 /* Create a handle bound to the CURRENT CUDA device.  Allocates a 256-byte

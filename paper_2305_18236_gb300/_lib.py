@@ -22,6 +22,8 @@ LAYOUTS = {"auto": LAYOUT_AUTO, "k_major": LAYOUT_K_MAJOR, "as_stored": LAYOUT_A
 SPLIT_AUTO, SPLIT_PREPASS, SPLIT_IN_KERNEL, SPLIT_IN_KERNEL_A, SPLIT_IN_KERNEL_B = 0, 1, 2, 3, 4
 SPLIT_PLACES = {"auto": SPLIT_AUTO, "prepass": SPLIT_PREPASS, "in_kernel": SPLIT_IN_KERNEL,
                 "in_kernel_a": SPLIT_IN_KERNEL_A, "in_kernel_b": SPLIT_IN_KERNEL_B}
+SPLITK_AUTO, SPLITK_LAUNCH = 0, 1
+SPLITK_REDUCES = {"auto": SPLITK_AUTO, "launch": SPLITK_LAUNCH}
 
 GEMM_OK = 0
 GEMM_ERR_ARG = -1
@@ -41,7 +43,7 @@ class gemm_config_t(ctypes.Structure):
     _fields_ = [("bn", _i32), ("bk", _i32), ("stages", _i32), ("split_k", _i32),
                 ("raster_group", _i32), ("max_ctas", _i32), ("promote_k", _i32),
                 ("cta_group", _i32), ("wait_poll_limit", _i64), ("operand_layout", _i32),
-                ("split_place", _i32)]
+                ("split_place", _i32), ("splitk_reduce", _i32)]
 
 
 class gemm_problem_t(ctypes.Structure):

@@ -239,6 +239,7 @@ TcLaunch plan_tc(const gemm_context* h, int nterms, int64_t M, int64_t N, int64_
         c.split_k = auto_split_k(((M + 127) / 128) * ((N + c.bn - 1) / c.bn),
                                  (K + c.bk - 1) / c.bk, h->num_sms);
     }
+    c.splitk_reduce = h->cfg.splitk_reduce;
     return c;
 }
 
@@ -673,6 +674,7 @@ gemm_status_t gemm_set_config(gemm_handle_t h, const gemm_config_t* cfg) {
         (c.operand_layout != GEMM_LAYOUT_AUTO && c.operand_layout != GEMM_LAYOUT_K_MAJOR &&
          c.operand_layout != GEMM_LAYOUT_AS_STORED) ||
         c.split_place < GEMM_SPLIT_AUTO || c.split_place > GEMM_SPLIT_IN_KERNEL_B ||
+        (c.splitk_reduce != GEMM_SPLITK_AUTO && c.splitk_reduce != GEMM_SPLITK_LAUNCH) ||
         (c.split_place >= GEMM_SPLIT_IN_KERNEL &&
          ((c.bn != 0 && c.bn != 256) || (c.bk != 0 && c.bk != 32) || c.cta_group == 2)))
         return fail_arg(h, 2);

@@ -15,7 +15,8 @@ struct TcLaunch {
     int stages = 0;          // 0 = deepest ring that fits
     int raster_group = 16;   // M tiles walked together
     int max_ctas = 0;        // 0 = one per SM
-    int split_k = 1;         // K slices (>1: partial sums + reduce kernel)
+    int split_k = 1;         // K slices (>1: partial sums, summed by a reduce kernel or in the GEMM)
+    int splitk_reduce = 0;   // split-K sum: 0 in the GEMM kernel when possible, 1 reduce launch
     long long poll_limit = 0;  // 0 = default
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
     int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)

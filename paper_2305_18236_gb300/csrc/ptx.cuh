@@ -275,6 +275,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Order this thread's async-proxy global accesses (completed TMA stores)
+// with its generic-proxy accesses, before a release makes them visible.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // 16-byte load and 8-byte store at a 32-bit shared-memory address.
 __device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
     float4 v;

@@ -86,6 +86,8 @@ struct TcParams {
     int count;
     int c_tma;  // epilogue writes through the C tensor map (beta == 0 or split-K partials)
     int fuse_ops;  // FUSE: bit 0 A, bit 1 B arrives as FP32 and is split in the kernel
+    int cluster_k;  // > 1: split-K slices of a tile run as one cluster and sum in the kernel
+    int sum_vec;    // cluster_k: the sum may use float4 (N, ldc % 4 == 0, C 16-byte aligned)
     int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
     // SYR2K (single launches): uplo 1 = lower, 2 = upper triangle of C (0 =
     // plain GEMM); syr_kb = K blocks of one product (the K loop runs twice as
@@ -464,6 +466,103 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
     }
 }
 
+// In-kernel split-K reduction (p.cluster_k = S > 1 CTAs per cluster, one
+// K slice each, all slices' partial tiles stored in p.partial): CTA rank r
+// sums tile rows [r R, r R + R), R = ceil(128 / S), over the slices in slice
+// order and writes C = alpha * sum (+ beta * C), the arithmetic of the
+// separate reduce kernel, so both give the same bits.  The partial tiles
+// come from L2; each thread keeps U x S 16-byte loads in flight (U = 8 / S
+// units of 4 columns) so the sum is not one L2 round trip per slice.  `ok`
+// false (a wait of this CTA gave up) skips the sum: the error is reported,
+// C is undefined.
+template <int BN, int S>
+__device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, int nt, int tid,
+                                                   int nthreads) {
+    constexpr int R = (kBM + S - 1) / S;
+    constexpr int U = S >= 8 ? 1 : 8 / S;
+    const int rank = int(blockIdx.x % unsigned(S));
+    const int r0 = mt * kBM + rank * R;
+    const int r1 = min(min(r0 + R, mt * kBM + kBM), p.M);
+    const int c0 = nt * BN;
+    const int cols = min(BN, p.N - c0);
+    if (r1 <= r0 || cols <= 0) return;
+    const size_t slab = size_t(p.M) * size_t(p.N);
+    const float alpha = p.alpha, beta = p.beta;
+    if (p.sum_vec) {  // N, ldc multiples of 4 and C 16-byte aligned
+        const int q4 = cols / 4;
+        const int units = (r1 - r0) * q4;
+        for (int i0 = tid; i0 < units; i0 += U * nthreads) {
+            float4 v[U][S];
+            size_t e[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = min(i0 + u * nthreads, units - 1);  // clamped: loaded, not stored
+                e[u] = size_t(r0 + i / q4) * size_t(p.N) + size_t(c0 + (i % q4) * 4);
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    v[u][q] = __ldcs(reinterpret_cast<const float4*>(p.partial + q * slab + e[u]));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + u * nthreads;
+                if (i >= units) break;
+                float4 acc = v[u][0];
+#pragma unroll
+                for (int q = 1; q < S; ++q) {
+                    acc.x += v[u][q].x;
+                    acc.y += v[u][q].y;
+                    acc.z += v[u][q].z;
+                    acc.w += v[u][q].w;
+                }
+                const int r = r0 + i / q4, c = c0 + (i % q4) * 4;
+                float4* cp = reinterpret_cast<float4*>(p.C + size_t(r) * size_t(p.ldc) + size_t(c));
+                float4 o = make_float4(alpha * acc.x, alpha * acc.y, alpha * acc.z, alpha * acc.w);
+                if (beta != 0.0f) {
+                    const float4 old = *cp;
+                    o.x = fmaf(beta, old.x, o.x);
+                    o.y = fmaf(beta, old.y, o.y);
+                    o.z = fmaf(beta, old.z, o.z);
+                    o.w = fmaf(beta, old.w, o.w);
+                }
+                *cp = o;
+            }
+        }
+    } else {
+        for (int i = tid; i < (r1 - r0) * cols; i += nthreads) {
+            const int r = r0 + i / cols, c = c0 + i % cols;
+            const size_t e = size_t(r) * size_t(p.N) + size_t(c);
+            float part[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) part[q] = p.partial[q * slab + e];
+            float acc = part[0];
+#pragma unroll
+            for (int q = 1; q < S; ++q) acc += part[q];
+            float* cp = p.C + size_t(r) * size_t(p.ldc) + size_t(c);
+            float o = alpha * acc;
+            if (beta != 0.0f) o = fmaf(beta, *cp, o);
+            *cp = o;
+        }
+    }
+}
+
+template <int BN>
+__device__ __noinline__ void cluster_sum_rows(const TcParams& p, int t, int tid, int nthreads,
+                                              bool ok) {
+    if (!ok) return;
+    const int rank = int(blockIdx.x % unsigned(p.cluster_k));
+    int mt, nt;
+    raster(t - rank * (p.num_m * p.num_n), p.num_m, p.num_n, p.raster_group, mt, nt);
+    switch (p.cluster_k) {
+        case 2: cluster_sum_rows_s<BN, 2>(p, mt, nt, tid, nthreads); break;
+        case 3: cluster_sum_rows_s<BN, 3>(p, mt, nt, tid, nthreads); break;
+        case 4: cluster_sum_rows_s<BN, 4>(p, mt, nt, tid, nthreads); break;
+        case 5: cluster_sum_rows_s<BN, 5>(p, mt, nt, tid, nthreads); break;
+        case 6: cluster_sum_rows_s<BN, 6>(p, mt, nt, tid, nthreads); break;
+        case 7: cluster_sum_rows_s<BN, 7>(p, mt, nt, tid, nthreads); break;
+        default: cluster_sum_rows_s<BN, 8>(p, mt, nt, tid, nthreads); break;
+    }
+}
+
 // FUSE (split precision only): the operands marked in p.fuse_ops are the
 // caller's FP32 matrices; TMA stages their FP32 tiles, converter warps split
 // them in place into the hi/lo atoms the MMA reads (split_group_in_place) and
@@ -521,6 +620,13 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // In-kernel split-K reduction: the grid is exactly the tile space and the
+    // cluster_k CTAs of a cluster take the K slices of one output tile (slice
+    // = rank in the cluster); otherwise CTAs walk the tiles persistently.
+    const bool cluster_sum = !GROUPED && p.cluster_k > 1;
+    const int t_first = cluster_sum ? int(blockIdx.x % unsigned(p.cluster_k)) * (p.num_m * p.num_n) +
+                                          int(blockIdx.x / unsigned(p.cluster_k))
+                                    : int(blockIdx.x);
 
     // Role dispatch, epilogue first: with FUSE the epilogue warpgroups raise
     // their register budget and the others (producer, MMA issuer, converters)
@@ -541,7 +647,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
         int g = 0;
         bool ok = true;
 #pragma unroll 1
-        for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+        for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
             const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
             const int kb0 = ti.kb0, kb1 = ti.kb1;
             const int chunk = PROMOTE ? p.chunk_kb : kb1 - kb0;
@@ -627,6 +733,18 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 }
             }
         }
+        if (cluster_sum) {
+            // this warp's partial-tile stores have landed; then every CTA of
+            // the cluster has stored its slice and the sum may read them all
+            if (lane == 0) {
+                bulk_wait_all();
+                fence_proxy_async_global();
+            }
+            __syncwarp();
+            cluster_sync();
+            cluster_sum_rows<BN>(p, t_first, (warp - EPI0) * 32 + lane, kEpiWarps * 32,
+                                 *abort_flag == 0);
+        }
     } else {
         if constexpr (FUSE) regs_dec<kFusedOtherRegs>();
         if (warp == 0) {
@@ -638,7 +756,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 int s = 0;                // ring slot of the next fill
                 uint32_t ph = 0;          // and its parity
                 bool ok = true;
-                for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
                     const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                     for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
                         if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
@@ -684,7 +802,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 uint32_t ph = 0;  // and its fill parity
                 bool ok = true;
                 const uint32_t slot0 = smem_u32(smem);
-                for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+                for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
                     const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                     const int kb0 = ti.kb0, kb1 = ti.kb1;
                     const int a_mn = ti.maj & 1, b_mn = (ti.maj >> 1) & 1;
@@ -762,7 +880,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
             uint32_t ph = 0;
             bool ok = true;
     #pragma unroll 1
-            for (int t = blockIdx.x; t < p.num_tiles && ok; t += gridDim.x) {
+            for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
                 const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                 const int wa = (ti.maj & 1) ? 64 : BK;         // row width of an A group
                 const int wb = ((ti.maj >> 1) & 1) ? 64 : BK;  // and of a B group
@@ -805,6 +923,10 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                     }
                 }
             }
+        }
+        if (cluster_sum) {  // the epilogue warps' barrier before their sum
+            __syncwarp();
+            cluster_sync();
         }
     }
 
@@ -1292,6 +1414,10 @@ bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
     return true;
 }
 
+// launch_variant's answer when a split-K cluster cannot be resident (not a
+// gemm_status_t: the caller falls back to the reduce launch)
+constexpr int kNoClusterRoom = -100;
+
 template <int BN, int BK, int NTERMS, bool PROMOTE, bool GROUPED, bool FUSE = false>
 int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
                    TcParams p, const TcLaunch& cfg, int num_sms, cudaStream_t stream) {
@@ -1306,11 +1432,50 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     auto kern = tc_gemm_kernel<BN, BK, NTERMS, PROMOTE, GROUPED, FUSE>;
     static std::atomic<uint64_t> smem_set{0};  // bit d: limit raised on device d
     if (!allow_max_smem(kern, smem_set)) return -4;
+    const int threads = FUSE ? kFusedThreads : kThreads;
+    if (!GROUPED && p.cluster_k > 1) {
+        // split-K slices summed in the kernel: one CTA per (tile, slice), the
+        // slices of a tile one cluster
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3(unsigned(p.num_tiles), 1, 1);
+        lc.blockDim = dim3(unsigned(threads), 1, 1);
+        lc.dynamicSmemBytes = size_t(smem);
+        lc.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = unsigned(p.cluster_k);
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        // a cluster of this many CTAs of this size must fit on the GPU
+        // (checked once per device and cluster size)
+        static std::atomic<uint64_t> fits_known{0}, fits{0};  // bit 8 d + k
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const uint64_t bit = (dev >= 0 && dev < 8) ? uint64_t(1) << (8 * dev + p.cluster_k - 1) : 0;
+        if (!bit || !(fits_known.load(std::memory_order_acquire) & bit)) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &lc) != cudaSuccess) {
+                cudaGetLastError();
+                n = 0;
+            }
+            if (!bit) {
+                if (n < 1) return kNoClusterRoom;
+            } else {
+                if (n >= 1) fits.fetch_or(bit, std::memory_order_relaxed);
+                fits_known.fetch_or(bit, std::memory_order_release);
+            }
+        }
+        if (bit && !(fits.load(std::memory_order_relaxed) & bit)) return kNoClusterRoom;
+        if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
+        return cudaGetLastError() == cudaSuccess ? 0 : -4;
+    }
     int ctas = num_sms;
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
     if (ctas < 1) ctas = 1;
-    kern<<<ctas, FUSE ? kFusedThreads : kThreads, smem, stream>>>(ta, tb, tc, p);
+    kern<<<ctas, threads, smem, stream>>>(ta, tb, tc, p);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
@@ -1515,13 +1680,28 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     // the kernel without promotion stores the same TMEM sums, bit for bit,
     // without holding them in registers first.
     const bool promote = nterms == 3 && cfg.promote_k > 0 && p.kb_per_split > p.chunk_kb;
-    const int rc = pair ? dispatch_pair<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
-                                               stream)
-                        : dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
-                                          stream);
+    // Split-K slices summed inside the GEMM kernel (a cluster of `split` CTAs
+    // per tile, at most 8 so the cluster size stays portable) instead of by
+    // a reduce launch; the same bits either way.  Only when every (tile,
+    // slice) has its own SM: with a second wave the clusters of the first
+    // must drain before those of the second start, which measured slower
+    // than persistent CTAs and the reduce launch (split-K 6 and 8 on
+    // (128, 8192, 8192): 0.050 / 0.059 ms against 0.046 / 0.041 ms).
+    if (split > 1 && split <= 8 && !pair && cfg.splitk_reduce != 1 &&
+        p.num_tiles <= num_sms) {
+        p.cluster_k = split;
+        p.sum_vec = N % 4 == 0 && ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+    }
+    int rc = pair ? dispatch_pair<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms,
+                                         stream)
+                  : dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream);
+    if (rc == kNoClusterRoom) {  // no room for such a cluster: persistent CTAs, reduce launch
+        p.cluster_k = 0;
+        rc = dispatch<false>(nterms, promote, bn, bk, ta, tb, tc, p, cfg, num_sms, stream);
+    }
     if (rc != 0) return rc;
     int n = 1;
-    if (split > 1) {
+    if (split > 1 && p.cluster_k == 0) {
         if (launch_splitk_reduce(M, N, split, partial, alpha, beta, C, ldc, stream) != cudaSuccess)
             return -4;
         ++n;

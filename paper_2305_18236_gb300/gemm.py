@@ -14,7 +14,8 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import LAYOUTS, MODES, SPLIT_PLACES, check, gemm_config_t, gemm_problem_t
+from ._lib import (LAYOUTS, MODES, SPLIT_PLACES, SPLITK_REDUCES, check, gemm_config_t,
+                   gemm_problem_t)
 
 __all__ = ["Gemm", "handle", "matmul", "matmul_bf16", "split_bf16", "gemm_from_host",
            "gemm_backward", "gemm_grouped", "GroupedPlan", "GemmFn", "sync"]
@@ -70,17 +71,20 @@ class Gemm:
     # -- configuration -------------------------------------------------
     def set_config(self, bn=0, bk=0, stages=0, split_k=0, raster_group=0, max_ctas=0,
                    promote_k=0, cta_group=0, wait_poll_limit=0, operand_layout="auto",
-                   split_place="auto"):
+                   split_place="auto", splitk_reduce="auto"):
         """operand_layout: "auto" (library choice), "as_stored" (MN-major tiles
         for operands stored K x rows) or "k_major" (every operand made
         K-contiguous first).  split_place (3xBF16): "auto", "prepass" (split
         pass before the kernel), "in_kernel" (the kernel splits FP32 tiles
         in shared memory), "in_kernel_a" / "in_kernel_b" (the kernel splits
-        A / B, the pass the other; matmul only)."""
+        A / B, the pass the other; matmul only).  splitk_reduce: "auto" (split-K
+        slices added inside the GEMM kernel where a cluster can hold them) or
+        "launch" (a second kernel adds them); the same bits either way."""
         layout = LAYOUTS[operand_layout] if isinstance(operand_layout, str) else operand_layout
         place = SPLIT_PLACES[split_place] if isinstance(split_place, str) else split_place
+        red = SPLITK_REDUCES[splitk_reduce] if isinstance(splitk_reduce, str) else splitk_reduce
         cfg = gemm_config_t(bn, bk, stages, split_k, raster_group, max_ctas, promote_k, cta_group,
-                            wait_poll_limit, layout, place)
+                            wait_poll_limit, layout, place, red)
         check(self.lib.gemm_set_config(self.h, ctypes.byref(cfg)), "gemm_set_config", self.h)
         self._ws_sizes.clear()
 
