@@ -97,11 +97,14 @@ bool pack_pays(int64_t M, int64_t N, int64_t K, bool pack_a, bool pack_b) {
 //    more than the kernel gains.
 // K slices of a launch with `tiles` output tiles and `kblocks` K blocks when
 // the handle leaves split-K to the library: few tiles and a long K are
-// sliced so that every SM gets work.
+// sliced so that every SM gets work, at least 4 K blocks a slice and at most
+// 8 slices, so that the GEMM kernel can sum them itself (a cluster of CTAs
+// per tile).  Measured at 1024^3 plain BF16 (16 K blocks of 64): 4 slices
+// 0.021 ms a call against 0.023 ms with 2.
 int auto_split_k(int64_t tiles, int64_t kblocks, int num_sms) {
     int64_t split = 1;
-    if (tiles * 2 <= num_sms && kblocks >= 16)
-        split = std::min<int64_t>({num_sms / std::max<int64_t>(tiles, 1), kblocks / 8, 16});
+    if (tiles * 2 <= num_sms && kblocks >= 8)
+        split = std::min<int64_t>({num_sms / std::max<int64_t>(tiles, 1), kblocks / 4, 8});
     return int(std::max<int64_t>(split, 1));
 }
 

@@ -492,20 +492,23 @@ __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, in
         const int q4 = cols / 4;
         const int units = (r1 - r0) * q4;
         for (int i0 = tid; i0 < units; i0 += U * nthreads) {
-            float4 v[U][S];
-            size_t e[U];
+            // every load of this batch (partials and C) before any store
+            float4 v[U][S], old[U];
+            float4* cp[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = min(i0 + u * nthreads, units - 1);  // clamped: loaded, not stored
-                e[u] = size_t(r0 + i / q4) * size_t(p.N) + size_t(c0 + (i % q4) * 4);
+                const int r = r0 + i / q4, c = c0 + (i % q4) * 4;
+                const size_t e = size_t(r) * size_t(p.N) + size_t(c);
 #pragma unroll
                 for (int q = 0; q < S; ++q)
-                    v[u][q] = __ldcs(reinterpret_cast<const float4*>(p.partial + q * slab + e[u]));
+                    v[u][q] = __ldcs(reinterpret_cast<const float4*>(p.partial + q * slab + e));
+                cp[u] = reinterpret_cast<float4*>(p.C + size_t(r) * size_t(p.ldc) + size_t(c));
+                old[u] = beta != 0.0f ? *cp[u] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int i = i0 + u * nthreads;
-                if (i >= units) break;
+                if (i0 + u * nthreads >= units) break;
                 float4 acc = v[u][0];
 #pragma unroll
                 for (int q = 1; q < S; ++q) {
@@ -514,17 +517,14 @@ __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, in
                     acc.z += v[u][q].z;
                     acc.w += v[u][q].w;
                 }
-                const int r = r0 + i / q4, c = c0 + (i % q4) * 4;
-                float4* cp = reinterpret_cast<float4*>(p.C + size_t(r) * size_t(p.ldc) + size_t(c));
                 float4 o = make_float4(alpha * acc.x, alpha * acc.y, alpha * acc.z, alpha * acc.w);
                 if (beta != 0.0f) {
-                    const float4 old = *cp;
-                    o.x = fmaf(beta, old.x, o.x);
-                    o.y = fmaf(beta, old.y, o.y);
-                    o.z = fmaf(beta, old.z, o.z);
-                    o.w = fmaf(beta, old.w, o.w);
+                    o.x = fmaf(beta, old[u].x, o.x);
+                    o.y = fmaf(beta, old[u].y, o.y);
+                    o.z = fmaf(beta, old[u].z, o.z);
+                    o.w = fmaf(beta, old[u].w, o.w);
                 }
-                *cp = o;
+                *cp[u] = o;
             }
         }
     } else {
@@ -542,6 +542,29 @@ __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, in
             if (beta != 0.0f) o = fmaf(beta, *cp, o);
             *cp = o;
         }
+    }
+}
+
+// The C rows of cluster_sum_rows, fetched into L2 ahead of its beta * C
+// reads (one prefetch per 128-byte line).
+template <int BN>
+__device__ __forceinline__ void cluster_sum_prefetch_c(const TcParams& p, int t, int tid,
+                                                       int nthreads) {
+    if (p.beta == 0.0f) return;
+    const int S = p.cluster_k;
+    const int rank = int(blockIdx.x % unsigned(S));
+    int mt, nt;
+    raster(t - rank * (p.num_m * p.num_n), p.num_m, p.num_n, p.raster_group, mt, nt);
+    const int R = (kBM + S - 1) / S;
+    const int r0 = mt * kBM + rank * R;
+    const int r1 = min(min(r0 + R, mt * kBM + kBM), p.M);
+    const int c0 = nt * BN;
+    const int cols = min(BN, p.N - c0);
+    if (r1 <= r0 || cols <= 0) return;
+    const int lines = (cols + 31) / 32;  // 128-byte lines per row (from the row's first column)
+    for (int i = tid; i < (r1 - r0) * lines; i += nthreads) {
+        const float* a = p.C + size_t(r0 + i / lines) * size_t(p.ldc) + size_t(c0 + (i % lines) * 32);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
     }
 }
 
@@ -646,6 +669,10 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
         float sum[PROMOTE ? COLS : 1];
         int g = 0;
         bool ok = true;
+        // the C rows this CTA's split-K sum will read: into L2 while the
+        // K loop runs
+        if (cluster_sum) cluster_sum_prefetch_c<BN>(p, t_first, (warp - EPI0) * 32 + lane,
+                                                    kEpiWarps * 32);
 #pragma unroll 1
         for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
             const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
