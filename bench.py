@@ -310,6 +310,17 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def gather_replicas(world, record):
+    """Every rank's record, in rank order (each replica's device and time)."""
+    if world == 1:
+        return [record]
+    import torch.distributed as dist
+
+    out = [None] * world
+    dist.all_gather_object(out, record)
+    return out
+
+
 def replica_tflops(flops_per_step, steps, ms_max, world):
     """Whole-job throughput of `world` independent replicas: every rank did
     `steps` steps of `flops_per_step` in at most `ms_max` milliseconds."""
@@ -623,6 +634,9 @@ def run_ours(args):
         "normwise_error": err,
         "peaks_source": peak_src,
     }
+    if world > 1:  # which GPU each replica ran on (distinct UUIDs: distinct devices)
+        line["replicas"] = gather_replicas(world, {"rank": rank, "local_rank": local,
+                                                   "uuid": uuid, "ms": ms})
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
