@@ -275,6 +275,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the preceding kernel of its stream still
+// runs; pdl_wait returns once that kernel has finished and its memory
+// writes are visible (at once for a kernel launched without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Order this thread's async-proxy global accesses (completed TMA stores)
 // with its generic-proxy accesses, before a release makes them visible.
 __device__ __forceinline__ void fence_proxy_async_global() {

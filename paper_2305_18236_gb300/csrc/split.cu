@@ -29,6 +29,13 @@ __device__ __forceinline__ void split1(float x, uint16_t& h, uint16_t& l) {
 
 __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) { return pack_bf16x2(a, b); }
 
+// Let a GEMM launched as this kernel's programmatic dependent start its set-up
+// (barriers, tensor memory) once every block of this kernel has begun; the
+// GEMM waits for this kernel's completion before reading what it wrote.
+__device__ __forceinline__ void allow_dependent_launch() {
+    asm volatile("griddepcontrol.launch_dependents;");
+}
+
 int grid_for(int64_t work, int per_block) {
     static int sms_of[64] = {};  // SM count per device, queried once
     int dev = 0, sms = 148;
@@ -92,6 +99,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(int64_t rows, int64_t c
                                                          uint16_t* __restrict__ hi,
                                                          uint16_t* __restrict__ lo, int64_t ldo,
                                                          int x_vec) {
+    allow_dependent_launch();
     split_rows_body(rows, cols, X, ldx, hi, lo, ldo, x_vec, blockIdx.x, gridDim.x);
 }
 
@@ -165,6 +173,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t co
                                                         uint16_t* __restrict__ hi,
                                                         uint16_t* __restrict__ lo, int64_t ldo) {
     __shared__ T tile[64][65];
+    allow_dependent_launch();
     transpose_body<T>(rows, cols, X, ldx, hi, lo, ldo, tile, blockIdx.x, gridDim.x);
 }
 
@@ -173,6 +182,7 @@ __global__ void __launch_bounds__(256) transpose_kernel(int64_t rows, int64_t co
 // takes one branch, so the transposing body's barriers stay block-uniform).
 __global__ void __launch_bounds__(256) split_pair_kernel(const SplitArg a, const SplitArg b) {
     __shared__ float tile[64][65];
+    allow_dependent_launch();
     const bool second = int(blockIdx.x) >= a.blocks;
     const SplitArg& j = second ? b : a;
     const int bid = second ? int(blockIdx.x) - a.blocks : int(blockIdx.x);

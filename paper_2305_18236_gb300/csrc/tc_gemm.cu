@@ -643,6 +643,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // launched as a dependent of the split pass: its planes are complete
+    // from here on (the set-up above overlapped the pass's tail)
+    pdl_wait();
     // In-kernel split-K reduction: the grid is exactly the tile space and the
     // cluster_k CTAs of a cluster take the K slices of one output tile (slice
     // = rank in the cluster); otherwise CTAs walk the tiles persistently.
@@ -1119,6 +1122,7 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    pdl_wait();  // as in the one-CTA kernel
 
     // One thread per producer role fills the ring; with SPLIT (plain BF16, whose
     // short stages make the copy issue the limit) warp 0 copies A and a second
@@ -1441,6 +1445,14 @@ bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
     return true;
 }
 
+// Launch attribute that lets the kernel start while the preceding kernel of
+// its stream (the split pass) finishes; the kernel's pdl_wait orders its
+// reads of that kernel's output.
+inline void set_pdl(cudaLaunchAttribute& a) {
+    a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a.val.programmaticStreamSerializationAllowed = 1;
+}
+
 // launch_variant's answer when a split-K cluster cannot be resident (not a
 // gemm_status_t: the caller falls back to the reduce launch)
 constexpr int kNoClusterRoom = -100;
@@ -1468,13 +1480,14 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
         lc.blockDim = dim3(unsigned(threads), 1, 1);
         lc.dynamicSmemBytes = size_t(smem);
         lc.stream = stream;
-        cudaLaunchAttribute attr[1];
+        cudaLaunchAttribute attr[2];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = unsigned(p.cluster_k);
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
+        if (cfg.pdl) set_pdl(attr[1]);
         lc.attrs = attr;
-        lc.numAttrs = 1;
+        lc.numAttrs = cfg.pdl ? 2 : 1;
         // a cluster of this many CTAs of this size must fit on the GPU
         // (checked once per device and cluster size)
         static std::atomic<uint64_t> fits_known{0}, fits{0};  // bit 8 d + k
@@ -1502,6 +1515,19 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
     if (ctas < 1) ctas = 1;
+    if (cfg.pdl) {
+        cudaLaunchConfig_t lc{};
+        lc.gridDim = dim3(unsigned(ctas), 1, 1);
+        lc.blockDim = dim3(unsigned(threads), 1, 1);
+        lc.dynamicSmemBytes = size_t(smem);
+        lc.stream = stream;
+        cudaLaunchAttribute attr[1];
+        set_pdl(attr[0]);
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
+        return cudaGetLastError() == cudaSuccess ? 0 : -4;
+    }
     kern<<<ctas, threads, smem, stream>>>(ta, tb, tc, p);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
@@ -1526,13 +1552,14 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
     lc.blockDim = dim3(pair_threads<NTERMS>(), 1, 1);
     lc.dynamicSmemBytes = smem;
     lc.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    if (cfg.pdl) set_pdl(attr[1]);
     lc.attrs = attr;
-    lc.numAttrs = 1;
+    lc.numAttrs = cfg.pdl ? 2 : 1;
     if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
