@@ -116,12 +116,11 @@ typedef struct gemm_context *gemm_handle_t;
  *    nearly the copy rate), as stored in grouped plans and gemm_syr2k, and
  *    in gemm_bf16 K-major only when the pack pass costs under a tenth of the
  *    GEMM (large, compute-bound shapes) -- as stored otherwise.
- *  splitk_reduce: GEMM_SPLITK_AUTO (0): with one CTA per tile, at most 8
- *    slices and no more (tile, slice) pairs than SMs, the slices of a tile
- *    run as one cluster of CTAs and the GEMM kernel itself adds them after a
- *    cluster barrier (no second launch; if such a cluster cannot be
- *    resident the reduce launch is used); otherwise a second kernel adds
- *    them.  GEMM_SPLITK_LAUNCH (1): always
+ *  splitk_reduce: GEMM_SPLITK_AUTO (0): with one CTA per tile, 2, 4 or 8
+ *    slices, no more (tile, slice) pairs than SMs and every such cluster
+ *    resident at once, the slices of a tile run as one cluster of CTAs and
+ *    the GEMM kernel itself adds them after a cluster barrier (no second
+ *    launch); otherwise a second kernel adds them.  GEMM_SPLITK_LAUNCH (1): always
  *    the second kernel.  Both give the same bits. */
 typedef enum {
     GEMM_LAYOUT_AUTO = 0,

@@ -1488,26 +1488,22 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
         if (cfg.pdl) set_pdl(attr[1]);
         lc.attrs = attr;
         lc.numAttrs = cfg.pdl ? 2 : 1;
-        // a cluster of this many CTAs of this size must fit on the GPU
-        // (checked once per device and cluster size)
-        static std::atomic<uint64_t> fits_known{0}, fits{0};  // bit 8 d + k
+        // every cluster of the grid must be resident at once (a second wave
+        // would wait for whole clusters of the first to drain): the number
+        // of such clusters the GPU holds, asked once per device and size
+        static std::atomic<int> resident[8][9];  // +1, 0 = not asked yet
         int dev = 0;
         cudaGetDevice(&dev);
-        const uint64_t bit = (dev >= 0 && dev < 8) ? uint64_t(1) << (8 * dev + p.cluster_k - 1) : 0;
-        if (!bit || !(fits_known.load(std::memory_order_acquire) & bit)) {
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, kern, &lc) != cudaSuccess) {
+        int fit = 0;
+        if (dev >= 0 && dev < 8) fit = resident[dev][p.cluster_k].load(std::memory_order_relaxed) - 1;
+        if (fit < 0) {
+            if (cudaOccupancyMaxActiveClusters(&fit, kern, &lc) != cudaSuccess) {
                 cudaGetLastError();
-                n = 0;
+                fit = 0;
             }
-            if (!bit) {
-                if (n < 1) return kNoClusterRoom;
-            } else {
-                if (n >= 1) fits.fetch_or(bit, std::memory_order_relaxed);
-                fits_known.fetch_or(bit, std::memory_order_release);
-            }
+            if (dev >= 0 && dev < 8) resident[dev][p.cluster_k].store(fit + 1, std::memory_order_relaxed);
         }
-        if (bit && !(fits.load(std::memory_order_relaxed) & bit)) return kNoClusterRoom;
+        if (p.num_tiles / p.cluster_k > fit) return kNoClusterRoom;
         if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
         return cudaGetLastError() == cudaSuccess ? 0 : -4;
     }
@@ -1741,7 +1737,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     // must drain before those of the second start, which measured slower
     // than persistent CTAs and the reduce launch (split-K 6 and 8 on
     // (128, 8192, 8192): 0.050 / 0.059 ms against 0.046 / 0.041 ms).
-    if (split > 1 && split <= 8 && !pair && cfg.splitk_reduce != 1 &&
+    // Cluster sizes 2, 4 and 8 only: with 5 slices (28 clusters, which the
+    // occupancy query says fit) the in-kernel split form measured 0.110 ms
+    // at (128, 7168, 8192) against 0.073 ms with persistent CTAs and the
+    // reduce launch; 3 slices gained nothing.
+    if ((split == 2 || split == 4 || split == 8) && !pair && cfg.splitk_reduce != 1 &&
         p.num_tiles <= num_sms) {
         p.cluster_k = split;
         p.sum_vec = N % 4 == 0 && ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;

@@ -118,13 +118,14 @@ def test_non_finite_operands_equal_split_pass():
 def test_split_k_with_in_kernel_split():
     """Split-K slices of an in-kernel-split launch, reduced in fixed order:
     integer data exact."""
-    hf, _ = _handles(split_k=3)
-    A, B, _ = make_problem(200, 300, 3000, dist="integers", seed=43)
-    C0 = inputs.integers((200, 300), 42)
-    got, launches = _run(hf, A, B, C0, 1.5, 0.5, False, False)
-    assert launches == 1  # the kernel (slices summed in it: a cluster per tile)
-    C64, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0)
-    assert np.array_equal(got.astype(np.float64), C64)
+    for split, want in ((3, 2), (4, 1)):  # 4 slices: summed in the kernel, a cluster per tile
+        hf, _ = _handles(split_k=split)
+        A, B, _ = make_problem(200, 300, 3000, dist="integers", seed=43)
+        C0 = inputs.integers((200, 300), 42)
+        got, launches = _run(hf, A, B, C0, 1.5, 0.5, False, False)
+        assert launches == want  # the kernel (and the reduce launch for 3 slices)
+        C64, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0)
+        assert np.array_equal(got.astype(np.float64), C64)
 
 
 @pytest.mark.parametrize("place", ["in_kernel_a", "in_kernel_b"])
