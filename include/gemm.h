@@ -84,7 +84,12 @@ typedef struct gemm_context *gemm_handle_t;
  *  stages:    shared-memory ring depth (2..8; clamped to what fits).
  *  split_k:   number of K slices (1 = none), each a partial sum; the partial
  *             sums are added in slice order, then C = alpha * sum + beta * C,
- *             as splitk_reduce says.
+ *             as splitk_reduce says.  Grouped plans choose per problem
+ *             instead: a problem whose one tile carries more K blocks than a
+ *             CTA's even share of the launch is cut into up to 8 slices
+ *             (problems of their own, then one reduce launch per such
+ *             problem), by the cost model, or by the autotuner when it times
+ *             faster; split_k 1 on the handle turns this off.
  *  raster_group: number of M tiles walked together before moving along N.
  *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).
  *  promote_k: GEMM_MODE_BF16X3 only: K elements summed in tensor memory

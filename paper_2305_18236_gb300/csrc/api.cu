@@ -582,6 +582,7 @@ bool handle_tile_auto(gemm_handle_t h) {
     return h->cfg.bn == 0 && h->cfg.bk == 0 && h->cfg.stages == 0 && h->cfg.cta_group == 0;
 }
 int handle_split_place(gemm_handle_t h) { return h->cfg.split_place; }
+int handle_split_k(gemm_handle_t h) { return h->cfg.split_k; }
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms) {
     // tile choice of the handle's configuration (problem-size independent
     // parts) for grouped launches

@@ -53,6 +53,18 @@ struct gemm_grouped_plan_s {
         float* C;
     };
     std::vector<Scale> scales;
+    // per-problem split-K: the slices' partial sums (plan-owned) and the
+    // reduces that add them into the callers' C after the grouped launch
+    float* partials = nullptr;
+    struct KReduce {
+        int64_t M, N, ldc;
+        int split;
+        float* P;
+        float alpha, beta;
+        float* C;
+    };
+    std::vector<KReduce> reduces;
+    int max_split = 1;
     // graph replay
     cudaGraphExec_t exec = nullptr;
     cudaStream_t exec_stream = nullptr;
@@ -201,6 +213,79 @@ std::vector<Candidate> seed_candidates(const std::vector<HostProb>& ps, int nter
     return out;
 }
 
+// Per-problem split-K (a grouped analogue of gemm()'s split-K for few-tile,
+// long-K problems): under a tile configuration, a problem whose one tile
+// carries more K blocks than a CTA's (or CTA pair's) even share of the whole
+// launch would finish last.  It is cut into S slices (up to 8, at least 4 K
+// blocks each); slice j is a problem of its own over K blocks [j per, (j+1)
+// per) that stores its raw partial sum (alpha 1, beta 0) in slab j of a
+// plan-owned buffer, and a reduce launch adds the slabs in slice order into C
+// with alpha and beta, as gemm()'s split-K does.  Returns S per problem.
+std::vector<int> straggler_splits(const std::vector<HostProb>& ps, const TcLaunch& cfg,
+                                  int num_sms) {
+    const int cg = cfg.cta_group == 2 ? 2 : 1;
+    const int bm = 128 * cg, bn = cfg.bn, bk = cfg.bk;
+    double units = 0.0;
+    for (const HostProb& q : ps)
+        units += double((q.M + bm - 1) / bm) * double((q.N + bn - 1) / bn) *
+                 double((q.K + bk - 1) / bk);
+    const double share = std::max(4.0, units / double(std::max(1, num_sms / cg)));
+    std::vector<int> out;
+    for (const HostProb& q : ps) {
+        const int64_t kb = (q.K + bk - 1) / bk;
+        int64_t sp = 1;
+        if (double(kb) > share) sp = std::min<int64_t>({8, int64_t(std::ceil(kb / share)), kb / 4});
+        out.push_back(int(std::max<int64_t>(sp, 1)));
+    }
+    return out;
+}
+
+// Slice [k0, k0 + k) of an operand's K range (a view of the same planes).
+TcOperand k_slice(const TcOperand& op, int64_t k0, int64_t k) {
+    TcOperand t = op;
+    t.base = op.base + (op.mn_major ? k0 * op.ld : k0);
+    t.k = k;
+    return t;
+}
+
+// The problems with every split problem replaced by its slices (their C the
+// partial slabs at `partials`, laid out problem by problem in order), and
+// the reduces that finish them.  Returns the float count of the slabs.
+size_t slice_problems(const std::vector<HostProb>& ps, const std::vector<int>& splits, int bk,
+                      float* partials, std::vector<HostProb>* out,
+                      std::vector<gemm_grouped_plan_s::KReduce>* reduces) {
+    out->clear();
+    if (reduces) reduces->clear();
+    size_t off = 0;
+    for (size_t i = 0; i < ps.size(); ++i) {
+        const HostProb& q = ps[i];
+        const int sp = splits.empty() ? 1 : splits[i];
+        if (sp <= 1) {
+            out->push_back(q);
+            continue;
+        }
+        const int64_t kb = (q.K + bk - 1) / bk;
+        const int64_t per = (kb + sp - 1) / sp;
+        const int slices = int((kb + per - 1) / per);
+        float* P = partials ? partials + off : nullptr;
+        for (int j = 0; j < slices; ++j) {
+            const int64_t k0 = j * per * bk, k1 = std::min<int64_t>(q.K, (j + 1) * per * bk);
+            HostProb sq = q;
+            sq.a = k_slice(q.a, k0, k1 - k0);
+            sq.b = k_slice(q.b, k0, k1 - k0);
+            sq.K = k1 - k0;
+            sq.C = P ? P + size_t(j) * size_t(q.M) * size_t(q.N) : nullptr;
+            sq.ldc = q.N;
+            sq.alpha = 1.0f;
+            sq.beta = 0.0f;
+            out->push_back(sq);
+        }
+        if (reduces) reduces->push_back({q.M, q.N, q.ldc, slices, P, q.alpha, q.beta, q.C});
+        off += size_t(slices) * size_t(q.M) * size_t(q.N);
+    }
+    return off;
+}
+
 std::string shape_key(int device_sms, int nterms, const std::vector<HostProb>& ps) {
     // order-independent signature: count and a hash of the sorted shapes
     std::vector<uint64_t> v;
@@ -229,8 +314,9 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
         *out = it->second;
         return true;
     }
-    // optional persistent cache: lines "key bn bk stages raster cta_group fuse"
-    // (a missing cta_group means one CTA, a missing fuse the split pass)
+    // optional persistent cache: lines "key bn bk stages raster cta_group fuse
+    // ksplit" (a missing cta_group means one CTA, a missing fuse the split
+    // pass, a missing ksplit no per-problem split-K)
     const char* path = getenv("GEMM_AUTOTUNE_CACHE");
     if (!path) return false;
     FILE* f = fopen(path, "r");
@@ -238,8 +324,9 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
     char line[256], k[128];
     bool found = false;
     while (fgets(line, sizeof line, f)) {
-        int bn, bk, st, rg, cg = 1, fu = 0;
-        const int n = sscanf(line, "%127s %d %d %d %d %d %d", k, &bn, &bk, &st, &rg, &cg, &fu);
+        int bn, bk, st, rg, cg = 1, fu = 0, ks = 0;
+        const int n =
+            sscanf(line, "%127s %d %d %d %d %d %d %d", k, &bn, &bk, &st, &rg, &cg, &fu, &ks);
         if (n < 5 || key != k) continue;
         out->bn = bn;
         out->bk = bk;
@@ -247,6 +334,7 @@ bool cache_lookup(const std::string& key, TcLaunch* out) {
         out->raster_group = rg;
         out->cta_group = cg == 2 ? 2 : 1;
         out->fuse = fu == 1 ? 3 : 0;
+        out->split_k = ks == 1 ? 2 : 1;  // 2: split stragglers
         found = true;
     }
     fclose(f);
@@ -261,8 +349,8 @@ void cache_store(const std::string& key, const TcLaunch& c) {
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
-            c.cta_group, c.fuse ? 1 : 0);
+    fprintf(f, "%s %d %d %d %d %d %d %d\n", key.c_str(), c.bn, c.bk, c.stages, c.raster_group,
+            c.cta_group, c.fuse ? 1 : 0, c.split_k > 1 ? 1 : 0);
     fclose(f);
 }
 
@@ -282,6 +370,7 @@ gemm_status_t upload(T** dst, const std::vector<T>& v, cudaStream_t s) {
 void free_plan(gemm_grouped_plan_s* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->ws) cudaFree(p->ws);
+    if (p->partials) cudaFree(p->partials);
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_probs) cudaFree(p->d_probs);
     if (p->d_maps) cudaFree(p->d_maps);
@@ -292,9 +381,11 @@ void free_plan(gemm_grouped_plan_s* p) {
 }
 
 // Time one configuration on (a subset of) the problems with C redirected to
-// plan-owned scratch and beta = 0, so the caller's C is never touched.
+// plan-owned scratch and beta = 0, so the caller's C is never touched; with
+// `reds`, the split-K reduces after the grouped launch are timed too.
 double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaunch& cfg,
-                      int* err_word, int num_sms, cudaStream_t s) {
+                      int* err_word, int num_sms, cudaStream_t s,
+                      const std::vector<gemm_grouped_plan_s::KReduce>* reds = nullptr) {
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
@@ -311,8 +402,14 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, s);
-            const int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, dt, int(sub.size()),
-                                                    tiles, err_word, num_sms, s);
+            int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, dt, int(sub.size()), tiles,
+                                              err_word, num_sms, s);
+            if (reds)
+                for (const auto& r : *reds)
+                    if (rc == 0 && gb300::launch_splitk_reduce(r.M, r.N, r.split, r.P, r.alpha,
+                                                               r.beta, r.C, r.ldc,
+                                                               s) != cudaSuccess)
+                        rc = -4;
             cudaEventRecord(e1, s);
             if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
                 best = -1.0;
@@ -332,6 +429,28 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
     return best;
 }
 
+// The same configuration with the straggler problems split along K (their
+// slices' partial sums in a temporary buffer, the reduces writing the
+// subset's scratch C); a negative time when there is nothing to split or no
+// memory.
+double time_split_variant(const std::vector<HostProb>& sub, int nterms, const TcLaunch& cfg,
+                          int* err_word, int num_sms, cudaStream_t s) {
+    const std::vector<int> splits = straggler_splits(sub, cfg, num_sms);
+    if (*std::max_element(splits.begin(), splits.end()) <= 1) return -1.0;
+    std::vector<HostProb> sliced;
+    const size_t floats = slice_problems(sub, splits, cfg.bk, nullptr, &sliced, nullptr);
+    float* buf = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&buf), floats * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    std::vector<gemm_grouped_plan_s::KReduce> reds;
+    slice_problems(sub, splits, cfg.bk, buf, &sliced, &reds);
+    const double ms = time_candidate(sliced, nterms, cfg, err_word, num_sms, s, &reds);
+    cudaFree(buf);
+    return ms;
+}
+
 gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
     for (const auto& sc : p->scales)
         if (gb300::launch_scale_c(sc.M, sc.N, sc.beta, sc.C, sc.ldc, s) != cudaSuccess)
@@ -344,7 +463,12 @@ gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
     const int rc = gb300::launch_tc_grouped(p->nterms, p->cfg, p->d_probs, p->d_maps,
                                             p->d_tile_prob, p->nprobs, p->total_tiles,
                                             p->err_word, p->num_sms, s);
-    return rc == 0 ? GEMM_OK : static_cast<gemm_status_t>(rc);
+    if (rc != 0) return static_cast<gemm_status_t>(rc);
+    for (const auto& r : p->reduces)
+        if (gb300::launch_splitk_reduce(r.M, r.N, r.split, r.P, r.alpha, r.beta, r.C, r.ldc, s) !=
+            cudaSuccess)
+            return GEMM_ERR_CUDA;
+    return GEMM_OK;
 }
 
 }  // namespace
@@ -359,6 +483,7 @@ void handle_set_launches(gemm_handle_t h, int n);
 TcLaunch handle_tc_config(gemm_handle_t h, int nterms);
 bool handle_tile_auto(gemm_handle_t h);
 int handle_split_place(gemm_handle_t h);
+int handle_split_k(gemm_handle_t h);
 }  // namespace gb300
 
 extern "C" {
@@ -548,6 +673,10 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             seed_candidates(shapes, nterms, p->num_sms, p->cfg, prepass_ok, fused_ok);
         if (!cands.empty()) p->cfg = cands.front().cfg;
     }
+    // straggler split-K unless the handle sets split_k 1 (never) or the
+    // autotuner decides (below)
+    const bool may_split = gb300::handle_split_k(h) != 1;
+    p->cfg.split_k = may_split ? 2 : 1;
     if ((flags & GEMM_GROUPED_AUTOTUNE) && !shapes.empty()) {
         const std::string key = shape_key(p->num_sms, nterms, shapes) +
                                 (prepass_ok ? "-p" : "") + (fused_ok ? "-f" : "");
@@ -559,6 +688,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
             p->cfg.raster_group = hit.raster_group;
             p->cfg.cta_group = hit.cta_group;
             p->cfg.fuse = hit.fuse;
+            p->cfg.split_k = may_split ? hit.split_k : 1;
             if (hit.fuse) p->cfg.kmajor = 0;
         } else {
             // Operands must be split before the pre-split candidates can be
@@ -659,6 +789,17 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
                     }
                 }
             }
+            // the best configuration with its straggler problems split along K
+            // (the pre-split placement only), kept if faster
+            best_cfg.split_k = 1;
+            if (best > 0.0 && !best_cfg.fuse && may_split) {
+                const double ms =
+                    time_split_variant(sub, nterms, best_cfg, p->err_word, p->num_sms, s);
+                if (ms > 0.0 && ms + split_ms * frac < best) {
+                    best = ms + split_ms * frac;
+                    best_cfg.split_k = 2;
+                }
+            }
             cudaFree(scratch);
             if (best > 0.0) {
                 p->cfg = best_cfg;
@@ -675,11 +816,32 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         p->nprobs = int(ps_f.size());
     }
 
+    // per-problem split-K of the straggler problems (pre-split placement)
+    std::vector<HostProb> sliced;
+    const std::vector<HostProb>* run_ps = p->cfg.fuse ? &ps_f : &ps;
+    if (!p->cfg.fuse && p->cfg.split_k > 1 && !ps.empty()) {
+        const std::vector<int> splits = straggler_splits(ps, p->cfg, p->num_sms);
+        const int most = *std::max_element(splits.begin(), splits.end());
+        if (most > 1) {
+            const size_t floats = slice_problems(ps, splits, p->cfg.bk, nullptr, &sliced, nullptr);
+            if (cudaMalloc(reinterpret_cast<void**>(&p->partials), floats * sizeof(float)) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                free_plan(p);
+                return GEMM_ERR_WORKSPACE;
+            }
+            slice_problems(ps, splits, p->cfg.bk, p->partials, &sliced, &p->reduces);
+            run_ps = &sliced;
+            p->nprobs = int(sliced.size());
+            p->max_split = most;
+        }
+    }
+    p->cfg.split_k = 1;  // the grouped kernel itself never slices K
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
     bool ok = true;
-    p->total_tiles = build_tables(p->cfg.fuse ? ps_f : ps, p->cfg, probs, maps, tile_prob, &ok);
+    p->total_tiles = build_tables(*run_ps, p->cfg, probs, maps, tile_prob, &ok);
     if (!ok) {
         free_plan(p);
         return GEMM_ERR_CUDA;
@@ -691,7 +853,8 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
         return st;
     }
     p->launches = int(p->scales.size()) + (p->split_tiles > 0 ? 1 : 0) +
-                  (p->split_tiles_t > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0);
+                  (p->split_tiles_t > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0) +
+                  int(p->reduces.size());
     *plan = p;
     return GEMM_OK;
 }
@@ -731,7 +894,7 @@ gemm_status_t gemm_grouped_plan_config(gemm_grouped_plan_t p, gemm_config_t* cfg
         cfg->bn = p->cfg.bn;
         cfg->bk = p->cfg.bk;
         cfg->stages = p->cfg.stages;
-        cfg->split_k = 1;
+        cfg->split_k = p->max_split;  // the most slices of any problem (1: none split)
         cfg->raster_group = p->cfg.raster_group;
         cfg->max_ctas = p->cfg.max_ctas;
         cfg->promote_k = p->cfg.promote_k > 0 ? p->cfg.promote_k : -1;

@@ -315,7 +315,7 @@ class GroupedPlan:
               "gemm_grouped_plan_config")
         names = {v: k for k, v in LAYOUTS.items()}
         places = {v: k for k, v in SPLIT_PLACES.items()}
-        return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages,
+        return {"bn": cfg.bn, "bk": cfg.bk, "stages": cfg.stages, "split_k": cfg.split_k,
                 "raster_group": cfg.raster_group, "cta_group": cfg.cta_group,
                 "operand_layout": names.get(cfg.operand_layout, cfg.operand_layout),
                 "split_place": places.get(cfg.split_place, cfg.split_place),

@@ -273,3 +273,93 @@ def test_grouped_config4_shapes_sampled():
         out = dev[i]["C"].cpu().numpy()[rows]
         assert oracle.normwise_error(out, C64, D) <= tol_exact("bf16x3", K)
     plan.close()
+
+
+def _straggler_problems(dist, seed):
+    """A few long-K problems with one or a few tiles each (they would finish
+    last in one persistent launch) among small ones."""
+    shapes = [(128, 512, 8192), (64, 256, 4096), (256, 768, 6144), (96, 96, 64), (64, 160, 96)]
+    out = []
+    for i, (M, N, K) in enumerate(shapes):
+        tA, tB = bool(i % 2), bool((i // 2) % 2)
+        alpha, beta = (1.5, 0.5) if i % 2 else (1.0, 0.0)
+        A = inputs.make(dist, (K, M) if tA else (M, K), seed + 3 * i, k=K)
+        B = inputs.make(dist, (N, K) if tB else (K, N), seed + 3 * i + 1, k=K)
+        C0 = inputs.integers((M, N), seed + 3 * i + 2) if dist == "integers" else \
+            inputs.uniform((M, N), seed + 3 * i + 2)
+        out.append(dict(A=A, B=B, C0=C0, transA=tA, transB=tB, alpha=alpha, beta=beta, M=M, N=N,
+                        K=K))
+    return out
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_grouped_straggler_split_k(autotune):
+    """Problems whose one tile carries more K blocks than a CTA's share of the
+    launch are split along K (slices in the launch, a reduce per split
+    problem, alpha and beta applied once): integer data exact, float data
+    within the oracle's bounds; graph replays equal eager runs."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = _straggler_problems("integers", 900)
+    dev = to_device(probs)
+    plan = g.GroupedPlan(dev, mode="bf16x3", autotune=autotune)
+    if not autotune:
+        assert plan.config()["split_k"] > 1  # the cost model splits the long-K problems
+    plan.run()
+    torch.cuda.synchronize()
+    for p, d in zip(probs, dev):
+        C64, _, _ = oracle.gemm(p["A"], p["B"], p["alpha"], p["beta"], p["C0"],
+                                transA=p["transA"], transB=p["transB"])
+        assert np.array_equal(d["C"].cpu().numpy().astype(np.float64), C64)
+    plan.close()
+
+    fprobs = _straggler_problems("uniform", 950)
+    d1, d2 = to_device(fprobs), to_device(fprobs)
+    eager = g.GroupedPlan(d1, mode="bf16x3")
+    graph = g.GroupedPlan(d2, mode="bf16x3", graph=True)
+    stream = torch.cuda.Stream()  # graph capture needs a non-default stream
+    with torch.cuda.stream(stream):
+        eager.run()
+        graph.run()
+    stream.synchronize()
+    check_against_oracle(fprobs, d1, "bf16x3")
+    for a, b in zip(d1, d2):
+        assert np.array_equal(a["C"].cpu().numpy().view(np.uint32),
+                              b["C"].cpu().numpy().view(np.uint32))
+    eager.close()
+    graph.close()
+
+
+def test_grouped_config4_set_has_no_straggler_split():
+    """On the uneven configuration-4 style set every tile is short against a
+    CTA's share of the launch: no problem is split."""
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = make_problems(64, 961, lo=64, hi=2048, ragged=False)
+    plan = g.GroupedPlan(to_device(probs), mode="bf16x3")
+    assert plan.config()["split_k"] == 1
+    plan.close()
+
+
+def test_grouped_straggler_split_off_by_handle():
+    """A handle with split_k 1 keeps every problem whole: the same straggler
+    set in one launch without reduces, integer data exact."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    probs = _straggler_problems("integers", 970)
+    dev = to_device(probs)
+    h = g.Gemm()
+    h.set_config(split_k=1)
+    plan = g.GroupedPlan(dev, mode="bf16x3", h=h)
+    assert plan.config()["split_k"] == 1
+    plan.run()
+    torch.cuda.synchronize()
+    for p, d in zip(probs, dev):
+        C64, _, _ = oracle.gemm(p["A"], p["B"], p["alpha"], p["beta"], p["C0"],
+                                transA=p["transA"], transB=p["transB"])
+        assert np.array_equal(d["C"].cpu().numpy().astype(np.float64), C64)
+    plan.close()
