@@ -30,15 +30,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t a, uint16_t b) {
 // half): hi = both rounded in one conversion; lo = bf16_rn(x - hi), cleared
 // in the half whose hi is Inf or NaN (exponent field all ones: adding 0x80
 // to the masked exponent 0x7f80 carries into bit 15 of that half, and into
-// nothing else).  Bit-identical to split_bf16_1 on each value.
+// nothing else).  A byte permute that replicates the top bit of bytes 1 and
+// 3 across their halves turns those two bits into the 16-bit clear masks.
+// Bit-identical to split_bf16_1 on each value.
 __device__ __forceinline__ void split_bf16_2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
     hi = *reinterpret_cast<const uint32_t*>(&h);
     const float d0 = x0 - __uint_as_float(hi << 16);
     const float d1 = x1 - __uint_as_float(hi & 0xffff0000u);
     const __nv_bfloat162 l = __floats2bfloat162_rn(d0, d1);
-    const uint32_t nonfinite = ((hi & 0x7f807f80u) + 0x00800080u) & 0x80008000u;
-    lo = *reinterpret_cast<const uint32_t*>(&l) & ~((nonfinite >> 15) * 0xffffu);
+    const uint32_t top = (hi & 0x7f807f80u) + 0x00800080u;  // bit 15 / 31: that half not finite
+    uint32_t clear;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(clear) : "r"(top));  // sign-replicate bytes 1, 3
+    lo = *reinterpret_cast<const uint32_t*>(&l) & ~clear;
 }
 
 }  // namespace gb300
