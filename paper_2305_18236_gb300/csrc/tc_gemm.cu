@@ -26,8 +26,8 @@
 // MMA issuer, warps 2-9 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31
 // and one half of the tile's columns); the plain-BF16 CTA-pair kernel adds
 // warp 10, which issues the B copies (352 threads).  With the in-kernel
-// split (FUSE, 512 threads) the epilogue is warps 4-11 and warps 2-3 and
-// 12-15 split FP32 stages into hi/lo in shared memory.
+// split (FUSE, 640 threads) the epilogue is warps 4-11 and warps 2-3 and
+// 12-19 split FP32 stages into hi/lo in shared memory.
 // Two accumulators (2 x BN TMEM columns) let the epilogue of tile i overlap
 // the MMAs of tile i+1.  Every wait is bounded (ptx.cuh); on expiry the
 // kernel records the error, drains its own copies and MMAs, frees TMEM and
@@ -52,17 +52,20 @@ namespace {
 constexpr int kBM = 128;
 constexpr int kEpiWarps = 8;               // warps 2..9
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue
-// In-kernel split (FUSE): 16 warps in four warpgroups -- warp 0 producer,
-// warp 1 MMA, warps 2-3 and 12-15 split FP32 stages into hi/lo in place,
-// warps 4-11 epilogue.  Registers are handed to a CTA per warpgroup; the
-// epilogue warpgroups take 200 a thread (128 running FP32 sums), the others
-// 56 (setmaxnreg): 256 x 200 + 256 x 56 = 65536 = 512 x 128.
-constexpr int kFusedThreads = 512;
-constexpr int kConvWarps = 6;
+// In-kernel split (FUSE): 20 warps in five warpgroups -- warp 0 producer,
+// warp 1 MMA, warps 2-3 and 12-19 split FP32 stages into hi/lo in place,
+// warps 4-11 epilogue.  Registers are handed to a CTA per warpgroup: the
+// block gets 96 a thread at launch (65536 / 640, in steps of 8), and
+// setmaxnreg moves them to the epilogue warpgroups, 168 a thread (128
+// running FP32 sums), from the others, 48: 256 x 168 + 384 x 48 = 640 x 96.
+constexpr int kFusedThreads = 640;
+constexpr int kConvWarps = 10;
 constexpr int kFusedEpi0 = 4;  // first epilogue warp
-constexpr int kFusedEpiRegs = 200;
-constexpr int kFusedOtherRegs = 56;
-static_assert(256 * kFusedEpiRegs + 256 * kFusedOtherRegs <= 65536, "register split");
+constexpr int kFusedEpiRegs = 168;
+constexpr int kFusedOtherRegs = 48;
+static_assert(256 * kFusedEpiRegs + (kFusedThreads - 256) * kFusedOtherRegs <=
+                  (65536 / kFusedThreads) / 8 * 8 * kFusedThreads,
+              "register split must fit what the block is launched with");
 constexpr int kMaxSmem = 232448;  // 227 KB opt-in dynamic shared memory per block
 
 struct TcParams {
