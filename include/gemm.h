@@ -87,8 +87,8 @@ typedef struct gemm_context *gemm_handle_t;
  *             as splitk_reduce says.  Grouped plans choose per problem
  *             instead: a problem whose one tile carries more K blocks than a
  *             CTA's even share of the launch is cut into up to 8 slices
- *             (problems of their own, then one reduce launch per such
- *             problem), by the cost model, or by the autotuner when it times
+ *             (problems of their own, then one reduce launch for all
+ *             of them), by the cost model, or by the autotuner when it times
  *             faster; split_k 1 on the handle turns this off.
  *  raster_group: number of M tiles walked together before moving along N.
  *  max_ctas:  upper bound on persistent CTAs (0 = one per SM).

@@ -64,6 +64,8 @@ struct gemm_grouped_plan_s {
         float* C;
     };
     std::vector<KReduce> reduces;
+    gb300::ReduceJob* d_reduces = nullptr;  // their device table: one reduce launch
+    long long reduce_units = 0;
     int max_split = 1;
     // graph replay
     cudaGraphExec_t exec = nullptr;
@@ -286,6 +288,31 @@ size_t slice_problems(const std::vector<HostProb>& ps, const std::vector<int>& s
     return off;
 }
 
+// The reduces as one launch's job table; returns the total units.
+long long reduce_table(const std::vector<gemm_grouped_plan_s::KReduce>& reds,
+                       std::vector<gb300::ReduceJob>* jobs) {
+    jobs->clear();
+    long long units = 0;
+    for (const auto& r : reds) {
+        gb300::ReduceJob j{};
+        j.P = r.P;
+        j.C = r.C;
+        j.M = r.M;
+        j.N = r.N;
+        j.ldc = r.ldc;
+        j.split = r.split;
+        j.alpha = r.alpha;
+        j.beta = r.beta;
+        j.vec = (r.N % 4 == 0) && (r.ldc % 4 == 0) &&
+                ((reinterpret_cast<uintptr_t>(r.C) & 15) == 0) &&
+                ((reinterpret_cast<uintptr_t>(r.P) & 15) == 0);
+        j.unit_start = units;
+        units += j.vec ? r.M * r.N / 4 : r.M * r.N;
+        jobs->push_back(j);
+    }
+    return units;
+}
+
 std::string shape_key(int device_sms, int nterms, const std::vector<HostProb>& ps) {
     // order-independent signature: count and a hash of the sorted shapes
     std::vector<uint64_t> v;
@@ -371,6 +398,7 @@ void free_plan(gemm_grouped_plan_s* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->ws) cudaFree(p->ws);
     if (p->partials) cudaFree(p->partials);
+    if (p->d_reduces) cudaFree(p->d_reduces);
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_probs) cudaFree(p->d_probs);
     if (p->d_maps) cudaFree(p->d_maps);
@@ -386,6 +414,9 @@ void free_plan(gemm_grouped_plan_s* p) {
 double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaunch& cfg,
                       int* err_word, int num_sms, cudaStream_t s,
                       const std::vector<gemm_grouped_plan_s::KReduce>* reds = nullptr) {
+    std::vector<gb300::ReduceJob> rjobs;
+    const long long runits = reds ? reduce_table(*reds, &rjobs) : 0;
+    gb300::ReduceJob* dr = nullptr;
     std::vector<GroupedProblem> probs;
     std::vector<CUtensorMap> maps;
     std::vector<int> tile_prob;
@@ -398,18 +429,16 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
     double best = -1.0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (upload(&dp, probs, s) == GEMM_OK && upload(&dm, maps, s) == GEMM_OK &&
-        upload(&dt, tile_prob, s) == GEMM_OK &&
+        upload(&dt, tile_prob, s) == GEMM_OK && upload(&dr, rjobs, s) == GEMM_OK &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
         for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(e0, s);
             int rc = gb300::launch_tc_grouped(nterms, cfg, dp, dm, dt, int(sub.size()), tiles,
                                               err_word, num_sms, s);
-            if (reds)
-                for (const auto& r : *reds)
-                    if (rc == 0 && gb300::launch_splitk_reduce(r.M, r.N, r.split, r.P, r.alpha,
-                                                               r.beta, r.C, r.ldc,
-                                                               s) != cudaSuccess)
-                        rc = -4;
+            if (rc == 0 && !rjobs.empty() &&
+                gb300::launch_splitk_reduce_grouped(dr, int(rjobs.size()), runits, num_sms, s) !=
+                    cudaSuccess)
+                rc = -4;
             cudaEventRecord(e1, s);
             if (rc != 0 || cudaEventSynchronize(e1) != cudaSuccess) {
                 best = -1.0;
@@ -426,6 +455,7 @@ double time_candidate(const std::vector<HostProb>& sub, int nterms, const TcLaun
     if (dp) cudaFree(dp);
     if (dm) cudaFree(dm);
     if (dt) cudaFree(dt);
+    if (dr) cudaFree(dr);
     return best;
 }
 
@@ -464,10 +494,10 @@ gemm_status_t enqueue(gemm_grouped_plan_s* p, cudaStream_t s) {
                                             p->d_tile_prob, p->nprobs, p->total_tiles,
                                             p->err_word, p->num_sms, s);
     if (rc != 0) return static_cast<gemm_status_t>(rc);
-    for (const auto& r : p->reduces)
-        if (gb300::launch_splitk_reduce(r.M, r.N, r.split, r.P, r.alpha, r.beta, r.C, r.ldc, s) !=
-            cudaSuccess)
-            return GEMM_ERR_CUDA;
+    if (p->d_reduces && gb300::launch_splitk_reduce_grouped(p->d_reduces, int(p->reduces.size()),
+                                                            p->reduce_units, p->num_sms,
+                                                            s) != cudaSuccess)
+        return GEMM_ERR_CUDA;
     return GEMM_OK;
 }
 
@@ -831,6 +861,12 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
                 return GEMM_ERR_WORKSPACE;
             }
             slice_problems(ps, splits, p->cfg.bk, p->partials, &sliced, &p->reduces);
+            std::vector<gb300::ReduceJob> rjobs;
+            p->reduce_units = reduce_table(p->reduces, &rjobs);
+            if ((st = upload(&p->d_reduces, rjobs, s)) != GEMM_OK) {
+                free_plan(p);
+                return st;
+            }
             run_ps = &sliced;
             p->nprobs = int(sliced.size());
             p->max_split = most;
@@ -854,7 +890,7 @@ gemm_status_t gemm_grouped_plan_create(gemm_handle_t h, gemm_mode_t mode,
     }
     p->launches = int(p->scales.size()) + (p->split_tiles > 0 ? 1 : 0) +
                   (p->split_tiles_t > 0 ? 1 : 0) + (p->nprobs > 0 ? 1 : 0) +
-                  int(p->reduces.size());
+                  (p->reduces.empty() ? 0 : 1);
     *plan = p;
     return GEMM_OK;
 }

@@ -190,4 +190,23 @@ cudaError_t launch_simt_syr2k(int uplo, int trans, int64_t N, int64_t K, float a
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int split_k, const float* P, float alpha,
                                  float beta, float* C, int64_t ldc, cudaStream_t stream);
 
+// One problem of a grouped split-K sum (device table entry): the same
+// C <- alpha * sum_s P[s] + beta * C over its `split` dense M x N slabs.
+// unit_start: the prefix sum of units (4 elements when vec, else 1) over the
+// preceding jobs; vec: N, ldc multiples of 4 and P, C 16-byte aligned.
+struct ReduceJob {
+    const float* P;
+    float* C;
+    long long M, N, ldc;
+    long long unit_start;
+    int split;
+    int vec;
+    float alpha, beta;
+};
+
+// Every job's sum in one launch (total_units units), with the arithmetic of
+// launch_splitk_reduce, so the two give the same bits.
+cudaError_t launch_splitk_reduce_grouped(const ReduceJob* dev_jobs, int njobs,
+                                         long long total_units, int num_sms, cudaStream_t stream);
+
 }  // namespace gb300

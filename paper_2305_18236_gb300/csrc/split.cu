@@ -561,6 +561,66 @@ cudaError_t launch_scale_c(int64_t M, int64_t N, float beta, float* C, int64_t l
     return cudaGetLastError();
 }
 
+namespace {
+
+// The grouped form: unit u belongs to the last job whose unit_start <= u
+// (binary search over the job table), then the per-element work of
+// splitk_reduce_kernel.
+__global__ void __launch_bounds__(256) splitk_reduce_grouped_kernel(
+    const ReduceJob* __restrict__ jobs, int njobs, long long total) {
+    for (long long u = blockIdx.x * 256ll + threadIdx.x; u < total; u += gridDim.x * 256ll) {
+        int lo = 0, hi = njobs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (jobs[mid].unit_start <= u)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const ReduceJob& j = jobs[lo];
+        const long long slab = j.M * j.N;
+        const long long e0 = u - j.unit_start;
+        if (j.vec) {
+            const long long e = e0 * 4;
+            const long long i = e / j.N, c = e - i * j.N;
+            float4 s = __ldcs(reinterpret_cast<const float4*>(j.P + e));
+            for (int q = 1; q < j.split; ++q) {
+                const float4 t = __ldcs(reinterpret_cast<const float4*>(j.P + q * slab + e));
+                s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+            }
+            float4* cp = reinterpret_cast<float4*>(j.C + i * j.ldc + c);
+            float4 o = make_float4(j.alpha * s.x, j.alpha * s.y, j.alpha * s.z, j.alpha * s.w);
+            if (j.beta != 0.0f) {
+                const float4 old = *cp;
+                o.x = fmaf(j.beta, old.x, o.x);
+                o.y = fmaf(j.beta, old.y, o.y);
+                o.z = fmaf(j.beta, old.z, o.z);
+                o.w = fmaf(j.beta, old.w, o.w);
+            }
+            *cp = o;
+        } else {
+            const long long i = e0 / j.N, c = e0 - i * j.N;
+            float s = j.P[e0];
+            for (int q = 1; q < j.split; ++q) s += j.P[q * slab + e0];
+            float* cp = j.C + i * j.ldc + c;
+            float o = j.alpha * s;
+            if (j.beta != 0.0f) o = fmaf(j.beta, *cp, o);
+            *cp = o;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_splitk_reduce_grouped(const ReduceJob* dev_jobs, int njobs,
+                                         long long total_units, int num_sms, cudaStream_t stream) {
+    if (njobs <= 0 || total_units <= 0) return cudaSuccess;
+    const long long want = (total_units + 255) / 256;
+    const int grid = int(std::max<long long>(1, std::min<long long>(want, 16ll * num_sms)));
+    splitk_reduce_grouped_kernel<<<grid, 256, 0, stream>>>(dev_jobs, njobs, total_units);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_splitk_reduce(int64_t M, int64_t N, int split_k, const float* P, float alpha,
                                  float beta, float* C, int64_t ldc, cudaStream_t stream) {
     const int vec = (N % 4 == 0) && (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
