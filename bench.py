@@ -747,7 +747,8 @@ def run_grouped(args):
     """512 problems, M, N, K uniform multiples of 32 in [64, 2048], FP32,
     3xBF16, alpha = 1, beta = 0: the library's plan (cost model) eager and
     graph-captured, one CTA per tile, the split pass or the in-kernel split
-    forced, and the autotuned plan."""
+    forced, and the autotuned plan; then a five-problem straggler set whose
+    long-K problems the plans split along K, against the set kept whole."""
     import numpy as np
     import torch
 
@@ -792,6 +793,30 @@ def run_grouped(args):
         hp.close()
         hf.close()
         hs.close()
+        # a straggler set: three long-K problems with one or a few tiles among
+        # small ones; the plans split them along K per problem (cost model or
+        # autotuner) -- against the same set kept whole (handle split_k 1)
+        st_shapes = [(128, 512, 8192), (64, 256, 4096), (256, 768, 6144), (96, 96, 64),
+                     (64, 160, 96)]
+        st_probs = []
+        for i, (M, N, K) in enumerate(st_shapes):
+            gen = torch.Generator(device="cuda").manual_seed(SEED + 1000 + i)
+            st_probs.append(dict(A=torch.rand((M, K), device="cuda", generator=gen) * 2 - 1,
+                                 B=torch.rand((K, N), device="cuda", generator=gen) * 2 - 1,
+                                 C=torch.empty((M, N), device="cuda")))
+        st_flops = sum(2.0 * M * N * K for (M, N, K) in st_shapes)
+        hw = g.Gemm()
+        hw.set_config(operand_layout=args.operand_layout, split_k=1)
+        stragglers = {}
+        for name, kw, hh in [("model_graph", dict(graph=True), h),
+                             ("tuned_graph", dict(autotune=True, graph=True), h),
+                             ("whole_graph", dict(graph=True), hw)]:
+            plan = g.GroupedPlan(st_probs, mode=args.mode, h=hh, **kw)
+            ms = _events_ms(plan.run, args.steps, args.warmup, stream)
+            stragglers[name] = {"ms": ms, "tflops": st_flops / ms / 1e9,
+                                "config": plan.config()}
+            plan.close()
+        hw.close()
     best = res["tuned_graph"]
     print(json.dumps({"metric": "grouped GEMM TFLOP/s, 512 problems (2MNK summed)",
                       "value": best["tflops"], "unit": "TFLOP/s", "n_gpus": 1,
@@ -800,7 +825,9 @@ def run_grouped(args):
                       "config": {"workload": "512 problems, M,N,K ~ 32*U{2..64}, FP32 U[-1,1]",
                                  "flops_per_step": flops,
                                  "operand_layout": args.operand_layout},
-                      "variants": res}), flush=True)
+                      "variants": res,
+                      "straggler_set": {"shapes": st_shapes, "variants": stragglers}}),
+          flush=True)
 
 
 def run_chain(args):
