@@ -542,7 +542,6 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     ob = fb ? f32_operand(B, ldb, N, K, transB == GEMM_OP_N) : operand_of(pb, b_hi, N, K, planes);
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
-    c2.pdl = launches > 0 ? 1 : 0;  // right after a split or pack launch on this stream
     float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
     int rc;
     {
@@ -789,7 +788,6 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
     }
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
-    c2.pdl = launches > 0 ? 1 : 0;  // right after a split or pack launch on this stream
     float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
     int rc;
     {
@@ -1087,7 +1085,6 @@ gemm_status_t gemm_syr2k(gemm_handle_t h, gemm_uplo_t uplo, gemm_op_t trans, int
     TcOperand xy = operand_of(sp.op, x_hi, N, K, 2 * sp.planes);
     xy.box_planes = sp.planes;
     int launches = 1;
-    cfg.pdl = 1;  // right after the split launch on this stream
     int rc;
     {
         ProfScope prof(h, s);

@@ -21,7 +21,6 @@ struct TcLaunch {
     int promote_k = 512;     // split-precision: K elements per TMEM chunk (0 = no promotion)
     int cta_group = 1;       // 2: CTA-pair kernel (256-row tiles, BN = 256 only)
     int kmajor = 0;          // 1: every operand K-major (transposing split / pack)
-    int pdl = 0;             // 1: may start while the preceding launch (a split pass) ends
     int fuse = 0;            // in-kernel split: bit 0 A, bit 1 B is FP32 (TcOperand::f32),
                              // split inside the kernel; the other operand is BF16 planes
 };

@@ -281,6 +281,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 // writes are visible (at once for a kernel launched without the attribute).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Let the next kernel of the stream, when launched with that attribute,
+// start its CTAs (they set up, then wait in pdl_wait for this grid to end).
+// A scheduling hint only: it orders no memory.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Order this thread's async-proxy global accesses (completed TMA stores)
 // with its generic-proxy accesses, before a release makes them visible.
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -325,6 +332,12 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
 __device__ __forceinline__ uint64_t l2_policy_evict_normal() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 

@@ -91,6 +91,7 @@ struct TcParams {
     int fuse_ops;  // FUSE: bit 0 A, bit 1 B arrives as FP32 and is split in the kernel
     int cluster_k;  // > 1: split-K slices of a tile run as one cluster and sum in the kernel
     int sum_vec;    // cluster_k: the sum may use float4 (N, ldc % 4 == 0, C 16-byte aligned)
+    int ring_epi;   // cluster_k with TMA partials: the ring holds every partial piece at once
     int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
     // SYR2K (single launches): uplo 1 = lower, 2 = upper triangle of C (0 =
     // plain GEMM); syr_kb = K blocks of one product (the K loop runs twice as
@@ -318,12 +319,15 @@ __device__ __forceinline__ void prefetch_c(const EpiInfo& ti, int row0, int col0
 // piece is lane l; its 16-byte chunk c sits at chunk c ^ (l % 8)), then one
 // lane issues a bulk tensor store to (col0, row0, z).  TMA clips the parts
 // of the box outside C.  Before rewriting the slab the lane waits until its
-// previous store has finished reading it.
+// previous store has finished reading it (`reuse`; a slab used once needs
+// no wait).
 __device__ __forceinline__ void store_piece_tma(const float* v, float* slab, int row0, int col0,
                                                 int z, float alpha, const CUtensorMap* map,
-                                                int lane) {
-    if (lane == 0) bulk_wait_read_all();
-    __syncwarp();
+                                                int lane, bool reuse = true) {
+    if (reuse) {
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
+    }
     uint8_t* row = reinterpret_cast<uint8_t*>(slab) + lane * 128;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
@@ -474,7 +478,7 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
 // sums tile rows [r R, r R + R), R = ceil(128 / S), over the slices in slice
 // order and writes C = alpha * sum (+ beta * C), the arithmetic of the
 // separate reduce kernel, so both give the same bits.  The partial tiles
-// come from L2; each thread keeps U x S 16-byte loads in flight (U = 8 / S
+// come from L2; each thread keeps U x S 16-byte loads in flight (U = 16 / S
 // units of 4 columns) so the sum is not one L2 round trip per slice.  `ok`
 // false (a wait of this CTA gave up) skips the sum: the error is reported,
 // C is undefined.
@@ -482,7 +486,7 @@ template <int BN, int S>
 __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, int nt, int tid,
                                                    int nthreads) {
     constexpr int R = (kBM + S - 1) / S;
-    constexpr int U = S >= 8 ? 1 : 8 / S;
+    constexpr int U = S >= 16 ? 1 : 16 / S;
     const int rank = int(blockIdx.x % unsigned(S));
     const int r0 = mt * kBM + rank * R;
     const int r1 = min(min(r0 + R, mt * kBM + kBM), p.M);
@@ -672,6 +676,12 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
         const int col_base = ((warp - EPI0) >> 2) * COLS;
         float* stg = staging + (warp - EPI0) * 32 * 33;
         float* slab = staging + (warp - EPI0) * 1024;  // 4 KB, 1024-byte aligned (TMA store)
+        // A cluster CTA owns one tile, so once its last chunk is in TMEM the
+        // ring is idle (every copy consumed by the MMAs): each partial piece
+        // then gets a slab of its own there and the stores go out back to
+        // back instead of waiting for one another
+        const bool ring = cluster_sum && p.ring_epi;
+        float* ring_slab = reinterpret_cast<float*>(smem) + (warp - EPI0) * PIECES * 1024;
         float sum[PROMOTE ? COLS : 1];
         int g = 0;
         bool ok = true;
@@ -736,8 +746,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                         if (p.c_tma) {
 #pragma unroll
                             for (int q = 0; q < PIECES; ++q)
-                                store_piece_tma(&sum[q * 32], slab, row0, col0 + q * 32, ti.ks,
-                                                e.alpha, &tmC, lane);
+                                store_piece_tma(&sum[q * 32], ring ? ring_slab + q * 1024 : slab,
+                                                row0, col0 + q * 32, ti.ks, e.alpha, &tmC, lane,
+                                                !ring);
                         } else {
 #pragma unroll
                             for (int q = 0; q < PIECES; ++q)
@@ -755,8 +766,8 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
                         const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
                         if (p.c_tma)
-                            store_piece_tma(v, slab, row0, col0 + q * 32, ti.ks, e.alpha, &tmC,
-                                            lane);
+                            store_piece_tma(v, ring ? ring_slab + q * 1024 : slab, row0,
+                                            col0 + q * 32, ti.ks, e.alpha, &tmC, lane, !ring);
                         else
                             store_piece(v, stg, row0, col0 + q * 32, e, lane);
                     }
@@ -775,15 +786,23 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
             }
             __syncwarp();
             cluster_sync();
-            cluster_sum_rows<BN>(p, t_first, (warp - EPI0) * 32 + lane, kEpiWarps * 32,
-                                 *abort_flag == 0);
+            // without FUSE the producer and MMA warps (threads 0-63) join
+            // the sum as threads 256-319
+            cluster_sum_rows<BN>(p, t_first, (warp - EPI0) * 32 + lane,
+                                 FUSE ? kEpiWarps * 32 : kThreads, *abort_flag == 0);
         }
     } else {
         if constexpr (FUSE) regs_dec<kFusedOtherRegs>();
         if (warp == 0) {
             // ------------------------------------------------ TMA producer
             if (lane == 0) {
-                const uint64_t pol = l2_policy_evict_last();
+                // L2 hints: an operand whose tiles only one tile row or
+                // column reads (B with a single M tile, A with a single N
+                // tile) streams through once and is evicted first; the
+                // other is kept for the tiles that read it again
+                const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
+                const uint64_t pol_a = !GROUPED && p.num_n == 1 ? once : keep;
+                const uint64_t pol_b = !GROUPED && p.num_m == 1 ? once : keep;
                 uint32_t filled = 0;      // bit s: slot s received a fill
                 uint32_t fill_par = 0;    // bit s: parity of slot s's latest fill
                 int s = 0;                // ring slot of the next fill
@@ -809,9 +828,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                         uint8_t* st = smem + s * S::STAGE;
                         mbar_arrive_expect_tx(&full[s], S::STAGE);
                         load_operand(st, ti.ma, &full[s], ti.maj & 1, kBM, S::MN_GROUP, kc * BK,
-                                     ti.mt * kBM, za, pol);
+                                     ti.mt * kBM, za, pol_a);
                         load_operand(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], (ti.maj >> 1) & 1,
-                                     BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol);
+                                     BN, S::MN_GROUP, kc * BK, ti.nt * BN, zb, pol_b);
                         filled |= 1u << s;
                         fill_par = (fill_par & ~(1u << s)) | (ph << s);
                         if (++s == stages) {
@@ -820,6 +839,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                         }
                     }
                 }
+                // every operand load of this CTA is issued: the next GEMM
+                // of the stream may start setting up on idle SMs
+                pdl_launch_dependents();
                 // Wait for every copy this thread started before the CTA may exit.
                 for (int s = 0; s < stages; ++s)
                     if (filled & (1u << s)) mbar_wait_drain(&full[s], (fill_par >> s) & 1, p.err);
@@ -960,6 +982,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
         if (cluster_sum) {  // the epilogue warps' barrier before their sum
             __syncwarp();
             cluster_sync();
+            if constexpr (!FUSE)
+                cluster_sum_rows<BN>(p, t_first, kEpiWarps * 32 + threadIdx.x, kThreads,
+                                     *abort_flag == 0);
         }
     }
 
@@ -1131,7 +1156,10 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
     // short stages make the copy issue the limit) warp 0 copies A and a second
     // warp copies B, otherwise warp 0 copies both.  Returns the stages filled.
     auto produce = [&](bool copy_a, bool copy_b) -> int {
-        const uint64_t pol = l2_policy_evict_last();
+        // L2 hints as in the one-CTA kernel (single pair-tile row: B once)
+        const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
+        const uint64_t pol_a = !GROUPED && p.num_n == 1 ? once : keep;
+        const uint64_t pol_b = !GROUPED && p.num_m == 1 ? once : keep;
         const uint32_t leader_full = mapa_shared(smem_u32(full), 0);
         const bool arm = rank == 0 && copy_a;  // the even A copier arms every phase
         int it = 0;       // stages filled
@@ -1150,11 +1178,11 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                 if (arm) mbar_arrive_expect_tx(&full[s], 2 * S::STAGE);  // all four parts
                 if (copy_a)
                     load_operand_pair(st, ti.ma, &full[s], bar, rank != 0, ti.maj & 1, kBM,
-                                      S::MN_GROUP, kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, pol);
+                                      S::MN_GROUP, kb * BK, ti.mt * 2 * kBM + int(rank) * kBM, pol_a);
                 if (copy_b)
                     load_operand_pair(st + S::PLANES * S::A_PLANE, ti.mb, &full[s], bar,
                                       rank != 0, (ti.maj >> 1) & 1, S::BNH, S::MN_GROUP, kb * BK,
-                                      ti.nt * BN + int(rank) * S::BNH, pol);
+                                      ti.nt * BN + int(rank) * S::BNH, pol_b);
                 if (++s == stages) {
                     s = 0;
                     ph ^= 1;
@@ -1181,6 +1209,7 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
         // ------------------------------------------------ TMA producer (both CTAs)
         if (lane == 0) {
             const int it = produce(true, !SPLIT);
+            pdl_launch_dependents();  // as in the one-CTA kernel
             if (rank != 0) {
                 report(1, it);
             } else {
@@ -1449,8 +1478,10 @@ bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
 }
 
 // Launch attribute that lets the kernel start while the preceding kernel of
-// its stream (the split pass) finishes; the kernel's pdl_wait orders its
-// reads of that kernel's output.
+// its stream finishes (a split pass, or a GEMM kernel, both of which allow
+// it once their loads are issued); the kernel's pdl_wait, before its first
+// global-memory access, orders it after that kernel's reads and writes.
+// Every GEMM kernel is launched with it.
 inline void set_pdl(cudaLaunchAttribute& a) {
     a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     a.val.programmaticStreamSerializationAllowed = 1;
@@ -1467,6 +1498,9 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     int stages = cfg.stages > 0 ? std::min(cfg.stages, S::max_stages()) : S::max_stages();
     if (stages < 2) stages = 2;
     p.stages = stages;
+    // split-K partial pieces of a cluster CTA: one 4 KB slab each in the ring
+    p.ring_epi = !GROUPED && p.cluster_k > 1 && p.c_tma &&
+                 stages * S::STAGE >= kEpiWarps * (BN / 64) * 4096;
     // Ask for enough shared memory that co-resident CTAs can never want more
     // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
@@ -1488,9 +1522,9 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
         attr[0].val.clusterDim.x = unsigned(p.cluster_k);
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        if (cfg.pdl) set_pdl(attr[1]);
+        set_pdl(attr[1]);
         lc.attrs = attr;
-        lc.numAttrs = cfg.pdl ? 2 : 1;
+        lc.numAttrs = 2;
         // every cluster of the grid must be resident at once (a second wave
         // would wait for whole clusters of the first to drain): the number
         // of such clusters the GPU holds, asked once per device and size
@@ -1514,20 +1548,16 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     if (cfg.max_ctas > 0) ctas = std::min(ctas, cfg.max_ctas);
     ctas = std::min(ctas, p.num_tiles);
     if (ctas < 1) ctas = 1;
-    if (cfg.pdl) {
-        cudaLaunchConfig_t lc{};
-        lc.gridDim = dim3(unsigned(ctas), 1, 1);
-        lc.blockDim = dim3(unsigned(threads), 1, 1);
-        lc.dynamicSmemBytes = size_t(smem);
-        lc.stream = stream;
-        cudaLaunchAttribute attr[1];
-        set_pdl(attr[0]);
-        lc.attrs = attr;
-        lc.numAttrs = 1;
-        if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
-        return cudaGetLastError() == cudaSuccess ? 0 : -4;
-    }
-    kern<<<ctas, threads, smem, stream>>>(ta, tb, tc, p);
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(unsigned(ctas), 1, 1);
+    lc.blockDim = dim3(unsigned(threads), 1, 1);
+    lc.dynamicSmemBytes = size_t(smem);
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    set_pdl(attr[0]);
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
@@ -1556,9 +1586,9 @@ int launch_pair_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUte
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    if (cfg.pdl) set_pdl(attr[1]);
+    set_pdl(attr[1]);
     lc.attrs = attr;
-    lc.numAttrs = cfg.pdl ? 2 : 1;
+    lc.numAttrs = 2;
     if (cudaLaunchKernelEx(&lc, kern, ta, tb, tc, p) != cudaSuccess) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
