@@ -204,6 +204,17 @@ __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Prefetch of a 3-D tile into L2 (no shared memory, no barrier): a
+// performance hint that moves no data into the CTA and orders nothing.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int32_t c0, int32_t c1,
+                                                int32_t c2, uint64_t cache_hint) {
+    asm volatile(
+        "cp.async.bulk.prefetch.tensor.3d.L2.global.tile.L2::cache_hint [%0, {%1, %2, %3}], %4;" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(c0), "r"(c1), "r"(c2), "l"(cache_hint)
+        : "memory");
+}
+
 // 3-D tiled load into this CTA's shared memory whose transaction bytes are
 // counted on an mbarrier of the CTA pair's even CTA (`bar_cluster`: a
 // shared::cluster address from mapa_shared), the cta_group::2 form.

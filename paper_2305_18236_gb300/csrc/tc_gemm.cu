@@ -92,6 +92,8 @@ struct TcParams {
     int cluster_k;  // > 1: split-K slices of a tile run as one cluster and sum in the kernel
     int sum_vec;    // cluster_k: the sum may use float4 (N, ldc % 4 == 0, C 16-byte aligned)
     int ring_epi;   // cluster_k with TMA partials: the ring holds every partial piece at once
+    int own_local;  // ring_epi, sum_vec, cluster_k 2 or 4: a CTA's own rows of its slice stay
+                    // in its ring (only it sums them) and are not stored
     int maj;    // single launches: bit 0 A MN-major, bit 1 B MN-major
     // SYR2K (single launches): uplo 1 = lower, 2 = upper triangle of C (0 =
     // plain GEMM); syr_kb = K blocks of one product (the K loop runs twice as
@@ -320,10 +322,10 @@ __device__ __forceinline__ void prefetch_c(const EpiInfo& ti, int row0, int col0
 // lane issues a bulk tensor store to (col0, row0, z).  TMA clips the parts
 // of the box outside C.  Before rewriting the slab the lane waits until its
 // previous store has finished reading it (`reuse`; a slab used once needs
-// no wait).
+// no wait).  `store` false leaves the piece in the slab only.
 __device__ __forceinline__ void store_piece_tma(const float* v, float* slab, int row0, int col0,
                                                 int z, float alpha, const CUtensorMap* map,
-                                                int lane, bool reuse = true) {
+                                                int lane, bool reuse = true, bool store = true) {
     if (reuse) {
         if (lane == 0) bulk_wait_read_all();
         __syncwarp();
@@ -336,7 +338,7 @@ __device__ __forceinline__ void store_piece_tma(const float* v, float* slab, int
                         alpha * v[4 * c + 3]);
     fence_proxy_async_smem();
     __syncwarp();
-    if (lane == 0) {
+    if (lane == 0 && store) {
         tma_store_3d(map, slab, col0, row0, z);
         bulk_commit_group();
     }
@@ -473,6 +475,29 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
     }
 }
 
+// The same boxes as load_operand, prefetched into L2.
+__device__ __forceinline__ void prefetch_operand(const CUtensorMap* map, int mn, int rows,
+                                                 int kcoord, int row0, uint64_t pol) {
+    if (!mn) {
+        tma_prefetch_3d(map, kcoord, row0, 0, pol);
+    } else {
+        for (int g = 0; g < rows / 64; ++g) tma_prefetch_3d(map, row0 + g * 64, kcoord, 0, pol);
+    }
+}
+
+// Byte offset, in the ring, of tile row lr / columns lc..lc+3 (lc a multiple
+// of 4) of a partial tile staged by the epilogue (ring_slab pieces: epilogue
+// warp w holds rows 32 ((w + epi0) % 4) .. +31 and column half w / 4, in
+// 4 KB pieces of 32 columns, 128-byte rows, 16-byte chunks swizzled by the
+// row's low three bits).
+template <int BN>
+__device__ __forceinline__ uint32_t ring_offset(int lr, int lc, int epi0) {
+    constexpr int COLS = BN / 2, PIECES = COLS / 32;
+    const int w = (lc / COLS) * 4 + (((lr >> 5) - epi0) & 3);
+    const int l = lr & 31, c = (lc & 31) >> 2;
+    return uint32_t(w * PIECES * 4096 + ((lc % COLS) >> 5) * 4096 + l * 128 + ((c ^ (l & 7)) << 4));
+}
+
 // In-kernel split-K reduction (p.cluster_k = S > 1 CTAs per cluster, one
 // K slice each, all slices' partial tiles stored in p.partial): CTA rank r
 // sums tile rows [r R, r R + R), R = ceil(128 / S), over the slices in slice
@@ -481,10 +506,11 @@ __device__ __forceinline__ void load_operand(uint8_t* dst, const CUtensorMap* ma
 // come from L2; each thread keeps U x S 16-byte loads in flight (U = 16 / S
 // units of 4 columns) so the sum is not one L2 round trip per slice.  `ok`
 // false (a wait of this CTA gave up) skips the sum: the error is reported,
-// C is undefined.
+// C is undefined.  `ring` (non-null with p.own_local): this CTA's own slice
+// rows come from the epilogue's slabs in its ring instead (not stored).
 template <int BN, int S>
 __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, int nt, int tid,
-                                                   int nthreads) {
+                                                   int nthreads, const uint8_t* ring, int epi0) {
     constexpr int R = (kBM + S - 1) / S;
     constexpr int U = S >= 16 ? 1 : 16 / S;
     const int rank = int(blockIdx.x % unsigned(S));
@@ -509,7 +535,10 @@ __device__ __forceinline__ void cluster_sum_rows_s(const TcParams& p, int mt, in
                 const size_t e = size_t(r) * size_t(p.N) + size_t(c);
 #pragma unroll
                 for (int q = 0; q < S; ++q)
-                    v[u][q] = __ldcs(reinterpret_cast<const float4*>(p.partial + q * slab + e));
+                    v[u][q] = ring && q == rank
+                                  ? *reinterpret_cast<const float4*>(
+                                        ring + ring_offset<BN>(r - mt * kBM, i % q4 * 4, epi0))
+                                  : __ldcs(reinterpret_cast<const float4*>(p.partial + q * slab + e));
                 cp[u] = reinterpret_cast<float4*>(p.C + size_t(r) * size_t(p.ldc) + size_t(c));
                 old[u] = beta != 0.0f ? *cp[u] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -575,21 +604,24 @@ __device__ __forceinline__ void cluster_sum_prefetch_c(const TcParams& p, int t,
     }
 }
 
+// `ring` (p.own_local): the CTA's shared-memory ring, where the epilogue
+// (first warp epi0) left this slice's partial rows of the CTA's share.
 template <int BN>
 __device__ __noinline__ void cluster_sum_rows(const TcParams& p, int t, int tid, int nthreads,
-                                              bool ok) {
+                                              bool ok, const uint8_t* ring, int epi0) {
     if (!ok) return;
     const int rank = int(blockIdx.x % unsigned(p.cluster_k));
     int mt, nt;
     raster(t - rank * (p.num_m * p.num_n), p.num_m, p.num_n, p.raster_group, mt, nt);
+    if (!p.own_local) ring = nullptr;
     switch (p.cluster_k) {
-        case 2: cluster_sum_rows_s<BN, 2>(p, mt, nt, tid, nthreads); break;
-        case 3: cluster_sum_rows_s<BN, 3>(p, mt, nt, tid, nthreads); break;
-        case 4: cluster_sum_rows_s<BN, 4>(p, mt, nt, tid, nthreads); break;
-        case 5: cluster_sum_rows_s<BN, 5>(p, mt, nt, tid, nthreads); break;
-        case 6: cluster_sum_rows_s<BN, 6>(p, mt, nt, tid, nthreads); break;
-        case 7: cluster_sum_rows_s<BN, 7>(p, mt, nt, tid, nthreads); break;
-        default: cluster_sum_rows_s<BN, 8>(p, mt, nt, tid, nthreads); break;
+        case 2: cluster_sum_rows_s<BN, 2>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        case 3: cluster_sum_rows_s<BN, 3>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        case 4: cluster_sum_rows_s<BN, 4>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        case 5: cluster_sum_rows_s<BN, 5>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        case 6: cluster_sum_rows_s<BN, 6>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        case 7: cluster_sum_rows_s<BN, 7>(p, mt, nt, tid, nthreads, ring, epi0); break;
+        default: cluster_sum_rows_s<BN, 8>(p, mt, nt, tid, nthreads, ring, epi0); break;
     }
 }
 
@@ -650,9 +682,6 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    // launched as a dependent of the split pass: its planes are complete
-    // from here on (the set-up above overlapped the pass's tail)
-    pdl_wait();
     // In-kernel split-K reduction: the grid is exactly the tile space and the
     // cluster_k CTAs of a cluster take the K slices of one output tile (slice
     // = rank in the cluster); otherwise CTAs walk the tiles persistently.
@@ -660,6 +689,24 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     const int t_first = cluster_sum ? int(blockIdx.x % unsigned(p.cluster_k)) * (p.num_m * p.num_n) +
                                           int(blockIdx.x / unsigned(p.cluster_k))
                                     : int(blockIdx.x);
+    // While the preceding kernel of the stream finishes, start pulling the
+    // first ring's worth of this CTA's first tile into L2.  Prefetches read
+    // nothing into the CTA, so they may come before pdl_wait: the loads that
+    // use the data are issued after it.
+    if (!GROUPED && p.uplo == 0 && threadIdx.x == 0 && t_first < p.num_tiles) {
+        const TileInfo ti = get_tile<GROUPED>(t_first, p, &tmA, &tmB);
+        const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
+        const int kb_end = min(ti.kb1, ti.kb0 + stages);
+        for (int kb = ti.kb0; kb < kb_end; ++kb) {
+            prefetch_operand(ti.ma, ti.maj & 1, kBM, kb * BK, ti.mt * kBM, p.num_n == 1 ? once : keep);
+            prefetch_operand(ti.mb, (ti.maj >> 1) & 1, BN, kb * BK, ti.nt * BN,
+                             p.num_m == 1 ? once : keep);
+        }
+    }
+    // launched as a dependent of a split pass or another GEMM: its writes
+    // are complete and visible from here on (the set-up above overlapped its
+    // tail)
+    pdl_wait();
 
     // Role dispatch, epilogue first: with FUSE the epilogue warpgroups raise
     // their register budget and the others (producer, MMA issuer, converters)
@@ -682,6 +729,9 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
         // back instead of waiting for one another
         const bool ring = cluster_sum && p.ring_epi;
         float* ring_slab = reinterpret_cast<float*>(smem) + (warp - EPI0) * PIECES * 1024;
+        // rows of this CTA's own share of the sum: kept in the ring, not stored
+        const bool keep = ring && p.own_local &&
+                          ew * 32 / (kBM / p.cluster_k) == int(blockIdx.x % unsigned(p.cluster_k));
         float sum[PROMOTE ? COLS : 1];
         int g = 0;
         bool ok = true;
@@ -748,7 +798,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                             for (int q = 0; q < PIECES; ++q)
                                 store_piece_tma(&sum[q * 32], ring ? ring_slab + q * 1024 : slab,
                                                 row0, col0 + q * 32, ti.ks, e.alpha, &tmC, lane,
-                                                !ring);
+                                                !ring, !keep);
                         } else {
 #pragma unroll
                             for (int q = 0; q < PIECES; ++q)
@@ -767,7 +817,8 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                         const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
                         if (p.c_tma)
                             store_piece_tma(v, ring ? ring_slab + q * 1024 : slab, row0,
-                                            col0 + q * 32, ti.ks, e.alpha, &tmC, lane, !ring);
+                                            col0 + q * 32, ti.ks, e.alpha, &tmC, lane, !ring,
+                                            !keep);
                         else
                             store_piece(v, stg, row0, col0 + q * 32, e, lane);
                     }
@@ -789,7 +840,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
             // without FUSE the producer and MMA warps (threads 0-63) join
             // the sum as threads 256-319
             cluster_sum_rows<BN>(p, t_first, (warp - EPI0) * 32 + lane,
-                                 FUSE ? kEpiWarps * 32 : kThreads, *abort_flag == 0);
+                                 FUSE ? kEpiWarps * 32 : kThreads, *abort_flag == 0, smem, EPI0);
         }
     } else {
         if constexpr (FUSE) regs_dec<kFusedOtherRegs>();
@@ -984,7 +1035,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
             cluster_sync();
             if constexpr (!FUSE)
                 cluster_sum_rows<BN>(p, t_first, kEpiWarps * 32 + threadIdx.x, kThreads,
-                                     *abort_flag == 0);
+                                     *abort_flag == 0, smem, EPI0);
         }
     }
 
@@ -1501,6 +1552,7 @@ int launch_variant(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     // split-K partial pieces of a cluster CTA: one 4 KB slab each in the ring
     p.ring_epi = !GROUPED && p.cluster_k > 1 && p.c_tma &&
                  stages * S::STAGE >= kEpiWarps * (BN / 64) * 4096;
+    p.own_local = p.ring_epi && p.sum_vec && (p.cluster_k == 2 || p.cluster_k == 4);
     // Ask for enough shared memory that co-resident CTAs can never want more
     // tensor memory than an SM has (512 columns), so tcgen05.alloc never waits.
     const int min_smem = S::TMEM_COLS == 512 ? 120 * 1024 : 80 * 1024;
