@@ -29,6 +29,14 @@
  * C <- beta * C without reading A or B; beta == 0 never reads C, so NaN or
  * Inf already in C does not reach the result.
  * A handle may be used by one host thread at a time.
+ * Stream order: the tensor-core GEMM kernels are launched with programmatic
+ * stream serialisation.  They may start setting up while the kernel before
+ * them on the stream finishes, but touch no global memory until it has
+ * completed.  Once a GEMM kernel has issued its operand loads it lets a
+ * following kernel that was launched with the same attribute start early.
+ * Such a kernel, like any dependent kernel, must wait for its prerequisite
+ * (cudaGridDependencySynchronize) before it reads C; kernels launched
+ * without the attribute are ordered as usual.
  */
 #ifndef GB300_GEMM_H
 #define GB300_GEMM_H
