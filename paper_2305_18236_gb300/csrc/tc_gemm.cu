@@ -859,9 +859,18 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 int s = 0;                // ring slot of the next fill
                 uint32_t ph = 0;          // and its parity
                 bool ok = true;
-                for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x) {
+                // Consecutive tiles of a CTA walk K in alternate directions:
+                // the CTAs move through a wave of tiles together, and the
+                // next wave of the raster reuses most of its operand panels,
+                // so starting it at the K blocks loaded last finds them still
+                // in L2.  (Only the order of a tile's K blocks changes, hence
+                // the order of its FP32 accumulation; it is fixed for a given
+                // grid.)
+                bool rev = false;  // K blocks of this tile in descending order
+                for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x, rev = !rev) {
                     const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
-                    for (int kb = ti.kb0; kb < ti.kb1; ++kb) {
+                    for (int kq = ti.kb0; kq < ti.kb1; ++kq) {
+                        const int kb = rev ? ti.kb0 + ti.kb1 - 1 - kq : kq;
                         if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                             ok = false;
                             break;
@@ -1217,9 +1226,12 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
         int s = 0;        // ring slot of the next fill
         uint32_t ph = 0;  // and its parity
         bool ok = true;
-        for (int t = pair; t < p.num_tiles && ok; t += npairs) {
+        // alternate K directions on consecutive tiles, as in the one-CTA kernel
+        bool rev = false;  // K blocks of this tile in descending order
+        for (int t = pair; t < p.num_tiles && ok; t += npairs, rev = !rev) {
             const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
-            for (int kb = ti.kb0; kb < ti.kb1; ++kb, ++it) {
+            for (int kq = ti.kb0; kq < ti.kb1; ++kq, ++it) {
+                const int kb = rev ? ti.kb0 + ti.kb1 - 1 - kq : kq;
                 if (!mbar_wait_bounded_cluster(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                     ok = false;
                     break;
