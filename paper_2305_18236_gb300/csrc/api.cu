@@ -250,6 +250,7 @@ struct WsPlan {
     size_t a_off = 0, b_off = 0, p_off = 0, total = 0;
     int planes = 1;
     int split = 1;
+    bool tail = false;  // p_off holds a CTA-pair launch's tail-split halves
 };
 
 // How one operand reaches the tensor cores after the split / pack pass.  An
@@ -323,9 +324,10 @@ TcOperand f32_operand(const float* X, int64_t ld, int64_t rows, int64_t K, bool 
 
 // Workspace of a tensor-core call: packed A and packed B (planes x the
 // operand's packed plane, BF16; plane size 0 = not packed), split-K partials
-// (split x M x N FP32).
+// (split x M x N FP32) or, with one K slice and num_sms > 0, the tail split's
+// half tiles of a CTA-pair launch.
 WsPlan plan_ws(int planes, int64_t a_plane, int64_t b_plane, int64_t M, int64_t N, int64_t K,
-               const TcLaunch& c) {
+               const TcLaunch& c, int num_sms = 0) {
     WsPlan w;
     w.planes = planes;
     size_t off = 0;
@@ -347,6 +349,13 @@ WsPlan plan_ws(int planes, int64_t a_plane, int64_t b_plane, int64_t M, int64_t 
     if (split > 1) {
         w.p_off = off;
         off += align_up(size_t(split) * M * N * 4);
+    } else if (num_sms > 0) {
+        const int64_t tail = gb300::tc_tail_floats(c, planes == 2 ? 3 : 1, M, N, K, 1, num_sms);
+        if (tail > 0) {
+            w.p_off = off;
+            off += align_up(size_t(tail) * 4);
+            w.tail = true;
+        }
     }
     w.total = off;
     return w;
@@ -519,7 +528,8 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     const bool fa = cfg.fuse & 1, fb = cfg.fuse & 2;
     const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, cfg);
     const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, cfg);
-    const WsPlan w = plan_ws(planes, fa ? 0 : pa.lay.plane, fb ? 0 : pb.lay.plane, M, N, K, cfg);
+    const WsPlan w = plan_ws(planes, fa ? 0 : pa.lay.plane, fb ? 0 : pb.lay.plane, M, N, K, cfg,
+                             h->num_sms);
     uint8_t* ws;
     gemm_status_t st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
@@ -542,7 +552,7 @@ gemm_status_t run_gemm(gemm_context* h, int transA, int transB, int64_t M, int64
     ob = fb ? f32_operand(B, ldb, N, K, transB == GEMM_OP_N) : operand_of(pb, b_hi, N, K, planes);
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
-    float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
+    float* partial = w.split > 1 || w.tail ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
     int rc;
     {
         ProfScope prof(h, s);
@@ -708,8 +718,21 @@ size_t gemm_workspace_size(gemm_handle_t h, gemm_mode_t mode, gemm_op_t transA, 
         const OpPlan pa = plan_op(M, K, transA == GEMM_OP_T, c);
         const OpPlan pb = plan_op(N, K, transB == GEMM_OP_N, c);
         bytes = std::max(bytes, plan_ws(nterms == 3 ? 2 : 1, (c.fuse & 1) ? 0 : pa.lay.plane,
-                                        (c.fuse & 2) ? 0 : pb.lay.plane, M, N, K, c)
+                                        (c.fuse & 2) ? 0 : pb.lay.plane, M, N, K, c, h->num_sms)
                                     .total);
+    }
+    if (nterms == 1) {
+        // gemm_bf16's own plan: its tiles (and so a tail split) may be wider;
+        // every MN-contiguous operand packed, beta zero or not
+        const bool a_kr = transA == GEMM_OP_T, b_kr = transB == GEMM_OP_N;
+        const gb300::PackedLayout la = gb300::packed_layout(M, K, false);
+        const gb300::PackedLayout lb = gb300::packed_layout(N, K, false);
+        for (int bz = 0; bz < 2; ++bz) {
+            const TcLaunch c = plan_tc(h, 1, M, N, K, Call::Bf16, a_kr, b_kr, bz != 0);
+            bytes = std::max(bytes, plan_ws(1, a_kr ? la.plane : 0, b_kr ? lb.plane : 0, M, N, K, c,
+                                            h->num_sms)
+                                        .total);
+        }
     }
     return bytes;
 }
@@ -765,7 +788,8 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
     if (!pack_b && misaligned(B, ldb)) return GEMM_ERR_ALIGN;
     const gb300::PackedLayout la = gb300::packed_layout(M, K, false);
     const gb300::PackedLayout lb = gb300::packed_layout(N, K, false);
-    const WsPlan w = plan_ws(1, pack_a ? la.plane : 0, pack_b ? lb.plane : 0, M, N, K, cfg);
+    const WsPlan w =
+        plan_ws(1, pack_a ? la.plane : 0, pack_b ? lb.plane : 0, M, N, K, cfg, h->num_sms);
     uint8_t* ws;
     st = get_ws(h, w.total, &ws);
     if (st != GEMM_OK) return st;
@@ -788,7 +812,7 @@ gemm_status_t gemm_bf16(gemm_handle_t h, gemm_op_t transA, gemm_op_t transB, int
     }
     TcLaunch c2 = cfg;
     c2.split_k = w.split;
-    float* partial = w.split > 1 ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
+    float* partial = w.split > 1 || w.tail ? reinterpret_cast<float*>(ws + w.p_off) : nullptr;
     int rc;
     {
         ProfScope prof(h, s);

@@ -92,10 +92,16 @@ int launch_tc_grouped(int nterms, const TcLaunch& cfg, const GroupedProblem* dev
 // does not exist).
 int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group = 1);
 
+// Floats of workspace a CTA-pair launch with one K slice uses to split the
+// tiles of a mostly idle last wave in two K halves (0: no tail split).
+int64_t tc_tail_floats(const TcLaunch& cfg, int nterms, int64_t M, int64_t N, int64_t K, int split,
+                       int num_sms);
+
 // C <- alpha * A_op B_op^T + beta * C where A_op is M x K and B_op is N x K
 // (both K-contiguous BF16); nterms = 1 (hi.hi) or 3 (lo.hi + hi.lo + hi.hi).
-// `partial` (split_k > 1) is split_k * M * N floats of workspace.
-// Returns 0 or a negative gemm_status_t value.
+// `partial`: split_k * M * N floats of workspace when split_k > 1; with one
+// K slice, null or the tc_tail_floats floats for a tail split (which then
+// adds a reduce launch).  Returns 0 or a negative gemm_status_t value.
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M, int64_t N,
                    int64_t K, float alpha, float beta, float* C, int64_t ldc, float* partial,
                    const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,

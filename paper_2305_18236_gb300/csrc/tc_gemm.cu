@@ -103,6 +103,17 @@ struct TcParams {
     int syr_kb;
     int syr_plane;
     int tri_r;  // BN / 128
+    // Tail split (CTA-pair launches with one K slice): when the tiles leave
+    // a last wave with at most half the pairs busy, tiles tail_base ..
+    // tail_base + tail_n - 1 are each computed in two K halves, K blocks
+    // [0, tail_kmid) by unit tail_base + i and [tail_kmid, k_blocks) by
+    // unit tail_base + tail_n + i, in parallel; each half stores its raw
+    // partial tile (2 kBM rows of BN floats) at tail_part + (2 i + half)
+    // tiles, and tail_reduce_kernel adds the two into C.  tail_n 0: none.
+    int tail_base;
+    int tail_n;
+    int tail_kmid;
+    float* tail_part;
 };
 
 template <int BN, int BK, int NTERMS>
@@ -145,6 +156,7 @@ struct EpiInfo {
     float* C;
     long long ldc;
     int uplo;  // 1: store only col <= row, 2: only col >= row (SYR2K)
+    int r_off = 0, c_off = 0;  // C holds the tile from row r_off, column c_off (tail partials)
 };
 
 // Local tile index -> (m tile, n tile): groups of `g` M tiles are walked
@@ -201,12 +213,24 @@ __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUt
         ti.ma = tmA;
         ti.mb = tmB;
     } else if (!GROUPED) {
+        int tt = t, half = -1;  // tail split: the tile of unit t and which K half
+        if (p.tail_n > 0 && t >= p.tail_base) {
+            const int u = t - p.tail_base;
+            half = u / p.tail_n;
+            tt = p.tail_base + u % p.tail_n;
+        }
         const int per_split = p.num_m * p.num_n;
-        ti.ks = t / per_split;
-        raster(t - ti.ks * per_split, p.num_m, p.num_n, p.raster_group, ti.mt, ti.nt);
+        ti.ks = tt / per_split;
+        raster(tt - ti.ks * per_split, p.num_m, p.num_n, p.raster_group, ti.mt, ti.nt);
         ti.kb0 = ti.ks * p.kb_per_split;
         ti.kb1 = min(ti.kb0 + p.kb_per_split, p.k_blocks);
         ti.prob = 0;
+        if (half >= 0) {  // prob: 1 + tail index, ks: the half
+            ti.kb0 = half ? p.tail_kmid : 0;
+            ti.kb1 = half ? p.k_blocks : p.tail_kmid;
+            ti.ks = half;
+            ti.prob = 1 + (tt - p.tail_base);
+        }
         ti.maj = p.maj;
         ti.ma = tmA;
         ti.mb = tmB;
@@ -277,7 +301,7 @@ __device__ __forceinline__ void store_piece(const float* v, float* stg, int row0
     if (e.uplo == 1) rlo = max(0, col - row0);           // col <= row
     if (e.uplo == 2) rhi = min(rhi, col - row0 + 1);      // col >= row
     if (col < e.N) {
-        float* base = e.C + size_t(row0) * size_t(e.ldc) + col;
+        float* base = e.C + size_t(row0 - e.r_off) * size_t(e.ldc) + (col - e.c_off);
         const size_t ldc = size_t(e.ldc);
         if (e.beta != 0.0f) {
 #pragma unroll
@@ -1058,6 +1082,69 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
     }
 }
 
+// The output side of a CTA-pair tile: get_epi's, or for a tail-split unit
+// its half's raw partial tile (alpha 1, beta 0) in the tail buffer.
+template <bool GROUPED, int BN>
+__device__ __forceinline__ EpiInfo pair_epi(const TileInfo& ti, const TcParams& p) {
+    EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
+    if (!GROUPED && ti.prob > 0) {
+        e.C = p.tail_part + size_t((ti.prob - 1) * 2 + ti.ks) * size_t(2 * kBM * BN);
+        e.ldc = BN;
+        e.alpha = 1.0f;
+        e.beta = 0.0f;
+        e.uplo = 0;
+        e.r_off = ti.mt * 2 * kBM;
+        e.c_off = ti.nt * BN;
+    }
+    return e;
+}
+
+// C = alpha (P0 + P1) + beta C over the tiles of a tail split (TcParams
+// tail_*), the two halves added in K order as the split-K reduce adds its
+// slices; block (i, y) takes every gridDim.y-th row chunk of tail tile i.
+// Launched as a dependent of the pair kernel that wrote the halves.
+template <int BN>
+__global__ void __launch_bounds__(256) tail_reduce_kernel(const TcParams p, int vec) {
+    pdl_wait();
+    const int i = int(blockIdx.x);
+    int mt, nt;
+    raster(p.tail_base + i, p.num_m, p.num_n, p.raster_group, mt, nt);
+    const int r0 = mt * 2 * kBM, c0 = nt * BN;
+    const int rows = min(2 * kBM, p.M - r0), cols = min(BN, p.N - c0);
+    const float* P0 = p.tail_part + size_t(2 * i) * size_t(2 * kBM * BN);
+    const float* P1 = P0 + size_t(2 * kBM * BN);
+    const float alpha = p.alpha, beta = p.beta;
+    if (vec) {  // N, ldc multiples of 4, C 16-byte aligned
+        const int q4 = cols / 4;
+        for (int idx = int(blockIdx.y * blockDim.x + threadIdx.x); idx < rows * q4;
+             idx += int(gridDim.y * blockDim.x)) {
+            const int lr = idx / q4, lc = (idx % q4) * 4;
+            const float4 a = __ldcs(reinterpret_cast<const float4*>(P0 + lr * BN + lc));
+            const float4 b = __ldcs(reinterpret_cast<const float4*>(P1 + lr * BN + lc));
+            float4* cp = reinterpret_cast<float4*>(p.C + size_t(r0 + lr) * size_t(p.ldc) + (c0 + lc));
+            float4 o = make_float4(alpha * (a.x + b.x), alpha * (a.y + b.y), alpha * (a.z + b.z),
+                                   alpha * (a.w + b.w));
+            if (beta != 0.0f) {
+                const float4 old = *cp;
+                o.x = fmaf(beta, old.x, o.x);
+                o.y = fmaf(beta, old.y, o.y);
+                o.z = fmaf(beta, old.z, o.z);
+                o.w = fmaf(beta, old.w, o.w);
+            }
+            *cp = o;
+        }
+    } else {
+        for (int idx = int(blockIdx.y * blockDim.x + threadIdx.x); idx < rows * cols;
+             idx += int(gridDim.y * blockDim.x)) {
+            const int lr = idx / cols, lc = idx % cols;
+            float* cp = p.C + size_t(r0 + lr) * size_t(p.ldc) + (c0 + lc);
+            float o = alpha * (P0[lr * BN + lc] + P1[lr * BN + lc]);
+            if (beta != 0.0f) o = fmaf(beta, *cp, o);
+            *cp = o;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- CTA pairs
 // The same GEMM with CTA pairs (cluster of two, tcgen05 cta_group::2): a
 // pair owns a 256 x BN output tile; each CTA stages its 128 rows of A and
@@ -1454,8 +1541,8 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                             mbar_arrive_remote(leader_acc_empty + uint32_t(buf) * 8u);
                     }
                     if (c0 + chunk >= kb1) {
-                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
-                        if (p.c_tma) {
+                        const EpiInfo e = pair_epi<GROUPED, BN>(ti, p);
+                        if (p.c_tma && ti.prob == 0) {  // (a tail half goes to its buffer)
 #pragma unroll
                             for (int q = 0; q < PIECES; ++q)
                                 store_piece_tma(&sum[q * 32], slab, row0, col0 + q * 32, ti.ks,
@@ -1475,11 +1562,11 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
                         float v[32];
 #pragma unroll
                         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-                        const EpiInfo e = get_epi<GROUPED>(ti.prob, ti.ks, p);
+                        const EpiInfo e = pair_epi<GROUPED, BN>(ti, p);
                         // 32-column pieces never cross a 128-column block
                         const int col = S::NSUB == 1 ? col0 + q * 32
                                                      : ti.nt * BN + wide_tile_col(col_base + q * 32);
-                        if (p.c_tma)
+                        if (p.c_tma && ti.prob == 0)
                             store_piece_tma(v, slab, row0, col, ti.ks, e.alpha, &tmC, lane);
                         else
                             store_piece(v, stg, row0, col, e, lane);
@@ -1782,6 +1869,51 @@ int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group) {
     return 1024 + stages * stage + 1024 + kEpiWarps * 32 * 33 * 4;
 }
 
+// Tail split of a CTA-pair launch with one K slice: the number of tiles in
+// a last wave that would keep at most half the pairs busy (0: no split).
+// The library then computes those tiles in two K halves on twice as many
+// pairs and adds the halves with tail_reduce_kernel, instead of leaving the
+// other pairs idle for a whole tile.  The same answer for the planner
+// (workspace) and the launch.
+int64_t tail_split_tiles(const TcLaunch& cfg, int nterms, int64_t M, int64_t N, int64_t K,
+                         int split, int num_sms) {
+    const bool wide = cfg.bn == 512 && cfg.cta_group == 2 && nterms == 1 && cfg.bk != 32;
+    const int bn = wide ? 512 : cfg.bn == 128 ? 128 : 256;
+    const int bk = wide ? 64 : cfg.bk == 64 ? 64 : 32;
+    if (!(cfg.cta_group == 2 && bn >= 256) || split > 1 || cfg.fuse) return 0;
+    const int64_t tiles = ((M + 2 * kBM - 1) / (2 * kBM)) * ((N + bn - 1) / bn);
+    int pairs = num_sms / 2;
+    if (cfg.max_ctas > 0) pairs = std::min(pairs, std::max(1, cfg.max_ctas / 2));
+    if (pairs < 2 || tiles < pairs || tiles + pairs > (1ll << 31) - 1) return 0;
+    const int64_t r = tiles % pairs;
+    if (r == 0 || 2 * r > pairs || (K + bk - 1) / bk < 2) return 0;
+    return r;
+}
+
+int64_t tc_tail_floats(const TcLaunch& cfg, int nterms, int64_t M, int64_t N, int64_t K, int split,
+                       int num_sms) {
+    const bool wide = cfg.bn == 512 && cfg.cta_group == 2 && nterms == 1 && cfg.bk != 32;
+    const int bn = wide ? 512 : cfg.bn == 128 ? 128 : 256;
+    return tail_split_tiles(cfg, nterms, M, N, K, split, num_sms) * 2 * (2 * kBM) * bn;
+}
+
+namespace {
+template <int BN>
+int launch_tail_reduce(const TcParams& p, cudaStream_t stream) {
+    const int vec = p.N % 4 == 0 && p.ldc % 4 == 0 && (reinterpret_cast<uintptr_t>(p.C) & 15) == 0;
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(unsigned(p.tail_n), 16, 1);
+    lc.blockDim = dim3(256, 1, 1);
+    lc.stream = stream;
+    cudaLaunchAttribute attr[1];
+    set_pdl(attr[0]);
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (cudaLaunchKernelEx(&lc, tail_reduce_kernel<BN>, p, vec) != cudaSuccess) return -4;
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+}  // namespace
+
 int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M, int64_t N,
                    int64_t K, float alpha, float beta, float* C, int64_t ldc, float* partial,
                    const TcLaunch& cfg, int* err_word, int num_sms, cudaStream_t stream,
@@ -1838,6 +1970,20 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     // occupancy query says fit) the in-kernel split form measured 0.110 ms
     // at (128, 7168, 8192) against 0.073 ms with persistent CTAs and the
     // reduce launch; 3 slices gained nothing.
+    // `partial` with one K slice: the tail-split buffer the planner reserved
+    const int64_t tail = partial && split == 1
+                             ? tail_split_tiles(cfg, nterms, M, N, K, split, num_sms)
+                             : 0;
+    if (tail > 0) {
+        const int chunk = std::max(1, p.chunk_kb);
+        int kmid = (p.k_blocks / 2 + chunk - 1) / chunk * chunk;  // promotion chunks kept whole
+        if (kmid >= p.k_blocks) kmid = p.k_blocks / 2;
+        p.tail_n = int(tail);
+        p.tail_base = p.num_tiles - p.tail_n;
+        p.tail_kmid = kmid;
+        p.tail_part = partial;
+        p.num_tiles += p.tail_n;
+    }
     if ((split == 2 || split == 4 || split == 8) && !pair && cfg.splitk_reduce != 1 &&
         p.num_tiles <= num_sms) {
         p.cluster_k = split;
@@ -1852,6 +1998,11 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
     }
     if (rc != 0) return rc;
     int n = 1;
+    if (p.tail_n > 0) {
+        if ((bn == 512 ? launch_tail_reduce<512>(p, stream) : launch_tail_reduce<256>(p, stream)) != 0)
+            return -4;
+        ++n;
+    }
     if (split > 1 && p.cluster_k == 0) {
         if (launch_splitk_reduce(M, N, split, partial, alpha, beta, C, ldc, stream) != cudaSuccess)
             return -4;
