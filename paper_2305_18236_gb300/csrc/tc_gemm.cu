@@ -105,14 +105,15 @@ struct TcParams {
     int tri_r;  // BN / 128
     // Tail split (CTA-pair launches with one K slice): when the tiles leave
     // a last wave with at most half the pairs busy, tiles tail_base ..
-    // tail_base + tail_n - 1 are each computed in two K halves, K blocks
-    // [0, tail_kmid) by unit tail_base + i and [tail_kmid, k_blocks) by
-    // unit tail_base + tail_n + i, in parallel; each half stores its raw
-    // partial tile (2 kBM rows of BN floats) at tail_part + (2 i + half)
-    // tiles, and tail_reduce_kernel adds the two into C.  tail_n 0: none.
+    // tail_base + tail_n - 1 are each computed in two halves of their K
+    // blocks, the even ones by unit tail_base + i and the odd ones by unit
+    // tail_base + tail_n + i, in parallel (both sweep the whole K range, so
+    // both find the previous wave's operand blocks in L2); each half stores
+    // its raw partial tile (2 kBM rows of BN floats) at tail_part +
+    // (2 i + half) tiles, and tail_reduce_kernel adds the two into C.
+    // tail_n 0: none.
     int tail_base;
     int tail_n;
-    int tail_kmid;
     float* tail_part;
 };
 
@@ -142,6 +143,7 @@ struct Shape {
 // Where output tile t sits: coordinates, K-block range, operand maps.
 struct TileInfo {
     int mt, nt, ks, kb0, kb1;
+    int kstep = 1, koff = 0;  // K block j of the tile is block koff + kstep * j of the operands
     int prob;  // problem index (grouped launches)
     int maj;   // bit 0: A MN-major, bit 1: B MN-major
     const CUtensorMap* ma;
@@ -225,9 +227,11 @@ __device__ __forceinline__ TileInfo get_tile(int t, const TcParams& p, const CUt
         ti.kb0 = ti.ks * p.kb_per_split;
         ti.kb1 = min(ti.kb0 + p.kb_per_split, p.k_blocks);
         ti.prob = 0;
-        if (half >= 0) {  // prob: 1 + tail index, ks: the half
-            ti.kb0 = half ? p.tail_kmid : 0;
-            ti.kb1 = half ? p.k_blocks : p.tail_kmid;
+        if (half >= 0) {  // prob: 1 + tail index, ks: the half (even or odd K blocks)
+            ti.kb0 = 0;
+            ti.kb1 = (p.k_blocks - half + 1) / 2;
+            ti.kstep = 2;
+            ti.koff = half;
             ti.ks = half;
             ti.prob = 1 + (tt - p.tail_base);
         }
@@ -894,7 +898,7 @@ __global__ void __launch_bounds__(FUSE ? kFusedThreads : kThreads, 1)
                 for (int t = t_first; t < p.num_tiles && ok; t += gridDim.x, rev = !rev) {
                     const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
                     for (int kq = ti.kb0; kq < ti.kb1; ++kq) {
-                        const int kb = rev ? ti.kb0 + ti.kb1 - 1 - kq : kq;
+                        const int kb = ti.koff + ti.kstep * (rev ? ti.kb0 + ti.kb1 - 1 - kq : kq);
                         if (!mbar_wait_bounded(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                             ok = false;
                             break;
@@ -1318,7 +1322,7 @@ __global__ void __launch_bounds__(pair_threads<NTERMS>(), 1)
         for (int t = pair; t < p.num_tiles && ok; t += npairs, rev = !rev) {
             const TileInfo ti = get_tile<GROUPED>(t, p, &tmA, &tmB);
             for (int kq = ti.kb0; kq < ti.kb1; ++kq, ++it) {
-                const int kb = rev ? ti.kb0 + ti.kb1 - 1 - kq : kq;
+                const int kb = ti.koff + ti.kstep * (rev ? ti.kb0 + ti.kb1 - 1 - kq : kq);
                 if (!mbar_wait_bounded_cluster(&empty[s], ph ^ 1, p.lim, abort_flag, p.err)) {
                     ok = false;
                     break;
@@ -1975,12 +1979,8 @@ int launch_tc_gemm(const TcOperand& a, const TcOperand& b, int nterms, int64_t M
                              ? tail_split_tiles(cfg, nterms, M, N, K, split, num_sms)
                              : 0;
     if (tail > 0) {
-        const int chunk = std::max(1, p.chunk_kb);
-        int kmid = (p.k_blocks / 2 + chunk - 1) / chunk * chunk;  // promotion chunks kept whole
-        if (kmid >= p.k_blocks) kmid = p.k_blocks / 2;
         p.tail_n = int(tail);
         p.tail_base = p.num_tiles - p.tail_n;
-        p.tail_kmid = kmid;
         p.tail_part = partial;
         p.num_tiles += p.tail_n;
     }
