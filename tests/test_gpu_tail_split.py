@@ -15,9 +15,12 @@ from tests.gpu_util import check_mode, make_problem, run_mode, to_dev
 pytestmark = pytest.mark.gpu
 
 # forced CTA pairs, 10 of them: 12 x 7 = 84 pair tiles of 256 x 256 leave a
-# last wave of 4 tiles, split into 8 half-tile units
+# last wave of 4 tiles (tile rows 8-11 of the last tile column), split into 8
+# half-tile units.  The split is taken when products x K >= 3 x 4096.
 CFG = dict(cta_group=2, max_ctas=20)
-M, N, K = 12 * 256 - 40, 7 * 256 - 20, 700  # ragged rows, columns and K
+M, N, K = 12 * 256 - 40, 7 * 256 - 20, 12288 + 40  # ragged rows, columns and K
+# sampled rows: some in the tail tiles (rows 2048 ..), some not
+ROWS = np.array([0, 700, 2047, 2048, 2300, 2600, 2900, M - 1])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,8 +47,8 @@ def test_integer_data_exact(mode, tA, tB):
     got = run_mode(mode, A, B, 1.5, 0.5, C0, tA, tB, h=h)
     # the operand split pass, the pair kernel and the tail reduce
     assert h.last_launch_count() == 3
-    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB)
-    assert np.array_equal(got.astype(np.float64), ref)
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.5, C0, transA=tA, transB=tB, rows=ROWS)
+    assert np.array_equal(got[ROWS].astype(np.float64), ref)
     h.close()
 
 
@@ -55,8 +58,20 @@ def test_no_tail_split_when_the_last_wave_is_more_than_half_full():
     h = _handle(cta_group=2, max_ctas=24)
     got = run_mode("bf16x3", A, B, 1.0, 0.0, None, False, False, h=h)
     assert h.last_launch_count() == 2
-    ref, _, _ = oracle.gemm(A, B)
-    assert np.array_equal(got.astype(np.float64), ref)
+    ref, _, _ = oracle.gemm(A, B, rows=ROWS)
+    assert np.array_equal(got[ROWS].astype(np.float64), ref)
+    h.close()
+
+
+def test_no_tail_split_for_short_k():
+    """3xBF16 at K = 2048: half a tile's K loop is worth less than the reduce
+    launch, so the last wave runs whole."""
+    A, B, _ = make_problem(M, N, 2048, dist="integers", seed=98)
+    h = _handle(**CFG)
+    got = run_mode("bf16x3", A, B, 1.0, 0.0, None, False, False, h=h)
+    assert h.last_launch_count() == 2
+    ref, _, _ = oracle.gemm(A, B, rows=ROWS)
+    assert np.array_equal(got[ROWS].astype(np.float64), ref)
     h.close()
 
 
@@ -64,7 +79,7 @@ def test_no_tail_split_when_the_last_wave_is_more_than_half_full():
 def test_float_data_within_bounds(dist):
     A, B, C0 = make_problem(M, N, K, dist=dist, seed=93, beta=0.5)
     h = _handle(**CFG)
-    check_mode("bf16x3", A, B, 1.5, 0.5, C0, False, False, h=h)
+    check_mode("bf16x3", A, B, 1.5, 0.5, C0, False, False, rows=ROWS, h=h)
     h.close()
 
 
@@ -81,8 +96,9 @@ def test_beta_zero_ignores_nan_c():
     g.matmul(to_dev(A), to_dev(B), C=C, alpha=2.0, beta=0.0, mode="bf16x3", h=h)
     torch.cuda.synchronize()
     assert h.last_launch_count() == 3
-    ref, _, _ = oracle.gemm(A, B, 2.0, 0.0)
-    assert np.array_equal(C.cpu().numpy().astype(np.float64), ref)
+    ref, _, _ = oracle.gemm(A, B, 2.0, 0.0, rows=ROWS)
+    assert np.array_equal(C.cpu().numpy()[ROWS].astype(np.float64), ref)
+    assert not torch.isnan(C).any()
     h.close()
 
 
