@@ -162,3 +162,28 @@ def test_graph_replay_equals_eager():
     torch.cuda.synchronize()
     assert torch.equal(C, eager)
     h.close()
+
+
+def test_wide_tiles_bf16_inputs_exact():
+    """gemm_bf16 on 256 x 512 pair tiles (beta 0: TMA-stored C outside the
+    tail): 12 x 7 = 84 tiles on 10 pairs, the last wave's 4 tiles split;
+    integer data exact on sampled rows, NaN in C never read."""
+    import torch
+
+    from paper_2305_18236_gb300 import gemm as g
+
+    Mw, Nw, Kw = 12 * 256 - 40, 7 * 512 - 24, 12288 + 64  # B rows 16-byte multiples
+    A = inputs.integers((Mw, Kw), 99)
+    B = inputs.integers((Kw, Nw), 100)
+    h = _handle(cta_group=2, bn=512, max_ctas=20, operand_layout="as_stored")
+    dA = torch.from_numpy(A).cuda().to(torch.bfloat16)
+    dB = torch.from_numpy(B).cuda().to(torch.bfloat16)
+    C = torch.full((Mw, Nw), float("nan"), device="cuda")
+    g.matmul_bf16(dA, dB, C=C, alpha=1.5, beta=0.0, h=h)
+    torch.cuda.synchronize()
+    assert h.last_launch_count() == 2  # the pair kernel (B read in place) and the tail reduce
+    rows = np.array([0, 2047, 2048, 2500, 3000, Mw - 1])
+    ref, _, _ = oracle.gemm(A, B, 1.5, 0.0, rows=rows)
+    assert np.array_equal(C.cpu().numpy()[rows].astype(np.float64), ref)
+    assert not torch.isnan(C).any()
+    h.close()
