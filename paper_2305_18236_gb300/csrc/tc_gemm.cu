@@ -1104,8 +1104,9 @@ __device__ __forceinline__ EpiInfo pair_epi(const TileInfo& ti, const TcParams& 
 }
 
 // C = alpha (P0 + P1) + beta C over the tiles of a tail split (TcParams
-// tail_*), the two halves added in K order as the split-K reduce adds its
-// slices; block (i, y) takes every gridDim.y-th row chunk of tail tile i.
+// tail_*): P0 the even K blocks' partial, P1 the odd ones', added in that
+// order with the split-K reduce's arithmetic; block (i, y) takes every
+// gridDim.y-th row chunk of tail tile i.
 // Launched as a dependent of the pair kernel that wrote the halves.
 template <int BN>
 __global__ void __launch_bounds__(256) tail_reduce_kernel(const TcParams p, int vec) {
@@ -1632,10 +1633,10 @@ bool allow_max_smem(Kernel kern, std::atomic<uint64_t>& done) {
 }
 
 // Launch attribute that lets the kernel start while the preceding kernel of
-// its stream finishes (a split pass, or a GEMM kernel, both of which allow
-// it once their loads are issued); the kernel's pdl_wait, before its first
-// global-memory access, orders it after that kernel's reads and writes.
-// Every GEMM kernel is launched with it.
+// its stream finishes (a split pass allows that from its start, a GEMM
+// kernel once its operand loads are issued); the kernel's pdl_wait, before
+// its first global-memory access, orders it after that kernel's reads and
+// writes.  Every GEMM kernel, and the tail reduce, is launched with it.
 inline void set_pdl(cudaLaunchAttribute& a) {
     a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
     a.val.programmaticStreamSerializationAllowed = 1;
@@ -1875,9 +1876,10 @@ int tc_smem_bytes(int nterms, int bn, int bk, int stages, int cta_group) {
 
 // Tail split of a CTA-pair launch with one K slice: the number of tiles in
 // a last wave that would keep at most half the pairs busy (0: no split).
-// The library then computes those tiles in two K halves on twice as many
-// pairs and adds the halves with tail_reduce_kernel, instead of leaving the
-// other pairs idle for a whole tile.  The same answer for the planner
+// The library then computes each of those tiles as two halves (its even and
+// its odd K blocks) on twice as many pairs and adds the halves with
+// tail_reduce_kernel, instead of leaving the other pairs idle for a whole
+// tile.  The same answer for the planner
 // (workspace) and the launch.
 int64_t tail_split_tiles(const TcLaunch& cfg, int nterms, int64_t M, int64_t N, int64_t K,
                          int split, int num_sms) {
